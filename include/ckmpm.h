@@ -1,0 +1,212 @@
+/*
+ * ckmpm.h -- C ABI of the GB300-native compact-kernel MPM (CK-MPM) step.
+ *
+ * Method: "CK-MPM: A Compact-Kernel Material Point Method" (arXiv 2412.10399).
+ * One time step (Sec. 3.2 pipeline, on the dual staggered grid of Sec. 4.2):
+ *   P2G   mass, APIC momentum (Sec. 4.4) and MLS stress force (Sec. 4.3.2,
+ *         Sec. 4.5) scattered onto both grids G- and G+ with the compact
+ *         kernel K1 (Sec. 4.1), two nodes per axis per grid;
+ *   grid  m v~ = m v + dt f per grid (Sec. 4.3.3), plus gravity and sticky
+ *         walls;
+ *   G2P   v and B gathered from both grids (Sec. 4.3.4, Sec. 4.4), F update
+ *         (Sec. 4.3.5), constitutive update (fixed-corotated, Drucker-Prager
+ *         return mapping; Sec. 3.2 step 4), advection (Sec. 3.2 step 5).
+ * A quadratic B-spline MLS-MPM path (single grid, 27 nodes) is built the same
+ * way for comparison (Sec. 5.2 / Sec. 6.2 comparison path).
+ *
+ * Conventions
+ *  - Node i of grid k in {-1 (G-), +1 (G+)} sits at (i - k/4) dx; node indices
+ *    run 0..res on every axis.  Quadratic nodes sit at i dx.
+ *  - Every call is made from one host thread per context; contexts are
+ *    independent.  No exception crosses this ABI and no kernel traps: device
+ *    errors set a status word that ckmpm_sync() reports.
+ *  - Pointers marked "host or device" are interpreted per the accompanying
+ *    is_device flag; device pointers must be on the context's device.
+ *  - Input arrays are borrowed for the duration of the call and copied; the
+ *    context owns all device state.  Output arrays are owned by the caller.
+ *  - All floating-point state is float32; parameters are given in double and
+ *    rounded once.
+ */
+#ifndef CKMPM_H
+#define CKMPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CKMPM_API __attribute__((visibility("default")))
+#else
+#define CKMPM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CKMPM_OK = 0,
+  CKMPM_EINVAL = 1,     /* invalid argument or state (message in ckmpm_last_error) */
+  CKMPM_ENOMEM = 2,     /* capacity or device memory exhausted (nothing changed) */
+  CKMPM_ECUDA = 3,      /* a CUDA runtime call failed */
+  CKMPM_EDOMAIN = 4,    /* a particle left the valid interior [0.5 dx, (res-0.5) dx) */
+  CKMPM_ENONFINITE = 5, /* a non-finite particle state was produced */
+  CKMPM_ETIMEOUT = 6,   /* a bounded device wait gave up */
+  CKMPM_EBUSY = 7,      /* operation not allowed now (e.g. during stream capture) */
+  CKMPM_ENOTFOUND = 8   /* unknown scene id */
+} ckmpm_status;
+
+typedef enum { CKMPM_KERNEL_CK = 0, CKMPM_KERNEL_QUADRATIC = 1 } ckmpm_kernel;
+typedef enum { CKMPM_FIXED_COROTATED = 0, CKMPM_DRUCKER_PRAGER = 1 } ckmpm_model;
+
+/* Constitutive parameters of one material.  Lame parameters are
+ * mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)).  Drucker-Prager
+ * uses Hencky elasticity and the cone alpha = sqrt(2/3) 2 sin(phi)/(3 - sin(phi))
+ * with cohesion 0 (klar2016, cited in Sec. 3.2). */
+typedef struct {
+  int model;            /* ckmpm_model */
+  double E;             /* Young's modulus [Pa] */
+  double nu;            /* Poisson ratio */
+  double rho;           /* density [kg/m^3]; particle mass = rho * dx^3 / ppc */
+  double friction_deg;  /* Drucker-Prager friction angle phi [deg] */
+} ckmpm_material;
+
+/* One simulation ("scene"): a cubic domain [0, res*dx]^3, y up. */
+typedef struct {
+  int64_t n;               /* number of particles (>= 1) */
+  const float* x;          /* n*3 positions, host or device; must lie in [0.5dx, (res-0.5)dx) */
+  const float* v;          /* n*3 velocities or NULL (zero), host or device */
+  const uint8_t* mat;      /* n material indices into materials[] or NULL (all 0) */
+  int is_device;           /* 1: x, v, mat are device pointers */
+  int res;                 /* cells per axis (4..4096) */
+  double dx;               /* cell size; a power of two keeps x/dx exact in float32 */
+  double dt;               /* time step */
+  double gravity[3];       /* m/s^2 added on nodes with mass */
+  double bc_cells;         /* sticky walls: v~ = 0 on nodes closer than bc_cells*dx to a wall */
+  int ppc;                 /* particles per cell used to sample; particle volume V0 = dx^3/ppc */
+  const ckmpm_material* materials; /* host array, copied */
+  int n_materials;         /* 1..255 */
+  /* Precision extension: the 3x3 SVD / polar decomposition of the constitutive
+   * update is redone in float64 where |det F| < fp64_j_tol, or
+   * sigma_min < fp64_cond_tol * sigma_max, or (sigma_i - sigma_j) <
+   * fp64_gap_tol * sigma_max for some pair.  Zero disables a criterion. */
+  double fp64_j_tol;
+  double fp64_cond_tol;
+  double fp64_gap_tol;
+} ckmpm_scene;
+
+/* Optional device-memory provider (for example a PyTorch caching allocator).
+ * alloc returns a device pointer aligned to 256 bytes or NULL. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, size_t bytes, void* user);
+  void* user;
+} ckmpm_allocator;
+
+/* Capacities of a multi-scene context (a "server"): all resident scenes step
+ * together in one launch per kernel over their concatenated block lists. */
+typedef struct {
+  int kernel;                  /* ckmpm_kernel; fixed for the context */
+  int64_t max_particles;       /* particle pool capacity */
+  int64_t max_keys;            /* particle-block key space (sum over scenes of ceil(res/4)^3) */
+  int64_t max_grid_blocks;     /* grid arena capacity in 4x4x4-node blocks (sum of (ceil(res/4)+1)^3) */
+  int max_scenes;              /* resident scene slots (<= 1024) */
+  int max_materials;           /* material table entries (<= 65535) */
+  int per_particle_E;          /* 1: keep a per-particle Young's modulus (differentiation) */
+  void* stream;                /* cudaStream_t to run on; NULL: the context creates one */
+  const ckmpm_allocator* allocator; /* NULL: cudaMalloc / cudaFree */
+} ckmpm_config;
+
+typedef struct ckmpm_ctx ckmpm_ctx;
+
+/* Particle and grid fields for readback / upload. */
+typedef enum {
+  CKMPM_FIELD_X = 0,      /* n*3 float positions (readback, upload) */
+  CKMPM_FIELD_V = 1,      /* n*3 float velocities (readback, upload) */
+  CKMPM_FIELD_B = 2,      /* n*9 float APIC matrix B, row-major (readback, upload) */
+  CKMPM_FIELD_C = 3,      /* n*9 float affine velocity gradient C = B D(x)^-1 (readback) */
+  CKMPM_FIELD_F = 4,      /* n*9 float (elastic) deformation gradient (readback, upload) */
+  CKMPM_FIELD_E = 5,      /* n float per-particle Young's modulus (needs per_particle_E) */
+  CKMPM_FIELD_GRID_M = 16,  /* per grid (G- then G+; one grid for quadratic) (res+1)^3 float
+                               node masses of the last ckmpm_probe_grids() */
+  CKMPM_FIELD_GRID_P = 17,  /* same layout, 3 floats per node: m v + dt f after P2G */
+  CKMPM_FIELD_GRID_V = 18   /* same layout, 3 floats per node: v~ after the grid update */
+} ckmpm_field;
+
+typedef struct {
+  int64_t n_particles;        /* particles in the pool (all scenes) */
+  int64_t n_particle_blocks;  /* non-empty particle blocks in the last step */
+  int64_t n_grid_blocks;      /* active grid blocks in the last step */
+  int64_t steps;              /* global steps taken */
+  int64_t fp64_particles;     /* particles that took the float64 SVD in the last step */
+  double ms_last_step;        /* device time of the last step (timing on) */
+  double ms_kernel[8];        /* average device ms per launch per kernel since the
+                                 last ckmpm_reset_timing(): 0 bin, 1 scatter,
+                                 2 p2g, 3 grid update, 4 g2p, 5 grid list */
+  int64_t launches_kernel[8]; /* launches counted in ms_kernel */
+  int64_t launches_per_step;  /* kernel launches issued by one step */
+} ckmpm_stats;
+
+/* Create a context holding one scene (scene id 0) with capacities equal to
+ * that scene.  kernel: ckmpm_kernel.  stream: cudaStream_t or NULL.
+ * Errors: EINVAL (bad scene), ENOMEM, ECUDA.  *out is NULL on error. */
+CKMPM_API ckmpm_status ckmpm_create(const ckmpm_scene* scene, int kernel, void* stream, ckmpm_ctx** out);
+
+/* Create an empty multi-scene context with the given capacities. */
+CKMPM_API ckmpm_status ckmpm_create_server(const ckmpm_config* cfg, ckmpm_ctx** out);
+
+/* Admit a scene into a context (continuous batching: takes effect at the next
+ * step; resident scenes keep running).  ENOMEM if any capacity would be
+ * exceeded (nothing changes).  *scene_id receives the scene's id. */
+CKMPM_API ckmpm_status ckmpm_admit(ckmpm_ctx* ctx, const ckmpm_scene* scene, int* scene_id);
+
+/* Remove a scene; its particles leave the pool at the next step and its
+ * capacity is reusable by later admissions. */
+CKMPM_API ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id);
+
+/* Enqueue n time steps of every resident scene on the context's stream.
+ * Asynchronous: device-side errors (EDOMAIN, ENONFINITE) surface at the next
+ * ckmpm_sync / ckmpm_readback.  Returns EINVAL for n < 0, ECUDA on a launch
+ * failure, or the sticky error of an earlier step. */
+CKMPM_API ckmpm_status ckmpm_step(ckmpm_ctx* ctx, int n);
+
+/* Wait for the context's stream and return the first device error (sticky). */
+CKMPM_API ckmpm_status ckmpm_sync(ckmpm_ctx* ctx);
+
+/* Run P2G and the grid update for the current state without advancing it,
+ * so that GRID_M / GRID_P / GRID_V can be read back. */
+CKMPM_API ckmpm_status ckmpm_probe_grids(ckmpm_ctx* ctx);
+
+/* Copy a field of one scene into dst (host or device), in the scene's
+ * original particle order.  bytes must equal the field size exactly.
+ * Synchronises the stream.  EINVAL on a size mismatch. */
+CKMPM_API ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, size_t bytes,
+                            int dst_is_device);
+
+/* Overwrite a particle field (X, V, B, F, E) of one scene from src (host or
+ * device), in the scene's original particle order.  bytes must equal the
+ * field size.  Synchronises the stream. */
+CKMPM_API ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* src, size_t bytes,
+                          int src_is_device);
+
+/* Number of particles of a scene, or -1. */
+CKMPM_API int64_t ckmpm_scene_particles(const ckmpm_ctx* ctx, int scene_id);
+
+/* Counters of the last step; timing adds CUDA events around every kernel
+ * (on the context's stream) and is off by default. */
+CKMPM_API ckmpm_status ckmpm_get_stats(ckmpm_ctx* ctx, ckmpm_stats* out);
+CKMPM_API ckmpm_status ckmpm_set_timing(ckmpm_ctx* ctx, int on);
+CKMPM_API ckmpm_status ckmpm_reset_timing(ckmpm_ctx* ctx);
+
+/* Release everything owned by the context.  NULL is accepted. */
+CKMPM_API ckmpm_status ckmpm_destroy(ckmpm_ctx* ctx);
+
+/* Human-readable description of the last error of ctx (never NULL). */
+CKMPM_API const char* ckmpm_last_error(const ckmpm_ctx* ctx);
+
+/* Library version string. */
+CKMPM_API const char* ckmpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CKMPM_H */

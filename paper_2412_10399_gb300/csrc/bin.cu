@@ -1,0 +1,223 @@
+// Per-step particle binning by particle block (counting sort on block keys).
+//
+// The histogram of the keys is produced by the previous G2P (or by admission
+// / re-keying).  One step then runs:
+//   scan_tiles  per 4096-key tile: particle count and non-empty key count
+//   scan_top    one CTA: exclusive scan over tiles; resets per-step counters
+//   scan_final  per key: offset and scatter cursor; non-empty keys become the
+//               particle-block list (in key order, so the list is
+//               deterministic) and flag the 2x2x2 grid blocks they touch;
+//               the next histogram is cleared
+//   scatter     perm[cursor[key]++] = particle (warp-aggregated atomics)
+//   glist       flagged grid blocks -> active grid-block list; flags cleared
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace ck {
+
+constexpr int kScanThreads = 256;
+constexpr int kPerThread = kScanTile / kScanThreads;  // 16
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(StepView v, BinScratch bs) {
+  const uint32_t base = blockIdx.x * kScanTile;
+  uint32_t c = 0, ne = 0;
+#pragma unroll
+  for (int q = 0; q < kPerThread; ++q) {
+    uint32_t k = base + q * kScanThreads + threadIdx.x;
+    if (k < v.n_keys) {
+      uint32_t x = v.cnt_cur[k];
+      c += x;
+      ne += x ? 1u : 0u;
+    }
+  }
+  __shared__ uint32_t sc[kScanThreads / 32], sn[kScanThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    ne += __shfl_down_sync(0xffffffffu, ne, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sc[threadIdx.x >> 5] = c;
+    sn[threadIdx.x >> 5] = ne;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tc = 0, tn = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+      tc += sc[w];
+      tn += sn[w];
+    }
+    bs.tile_cnt[blockIdx.x] = tc;
+    bs.tile_ne[blockIdx.x] = tn;
+  }
+}
+
+// Exclusive scan of (tile_cnt, tile_ne) in place by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_top(StepView v, BinScratch bs, uint32_t ntiles) {
+  __shared__ uint32_t wc[32], wn[32];
+  __shared__ uint32_t carry_c, carry_n;
+  if (threadIdx.x == 0) {
+    carry_c = 0;
+    carry_n = 0;
+    *v.n_g = 0;
+    *v.fp64_count = 0ull;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t b0 = 0; b0 < ntiles; b0 += 1024) {
+    uint32_t i = b0 + threadIdx.x;
+    uint32_t c = i < ntiles ? bs.tile_cnt[i] : 0u;
+    uint32_t n = i < ntiles ? bs.tile_ne[i] : 0u;
+    uint32_t ic = c, in = n;  // inclusive within warp
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t yc = __shfl_up_sync(0xffffffffu, ic, o);
+      uint32_t yn = __shfl_up_sync(0xffffffffu, in, o);
+      if (lane >= o) {
+        ic += yc;
+        in += yn;
+      }
+    }
+    if (lane == 31) {
+      wc[warp] = ic;
+      wn[warp] = in;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t xc = wc[lane], xn = wn[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t yc = __shfl_up_sync(0xffffffffu, xc, o);
+        uint32_t yn = __shfl_up_sync(0xffffffffu, xn, o);
+        if (lane >= o) {
+          xc += yc;
+          xn += yn;
+        }
+      }
+      wc[lane] = xc;
+      wn[lane] = xn;
+    }
+    __syncthreads();
+    uint32_t pc = (warp ? wc[warp - 1] : 0u) + ic - c + carry_c;
+    uint32_t pn = (warp ? wn[warp - 1] : 0u) + in - n + carry_n;
+    if (i < ntiles) {
+      bs.tile_cnt[i] = pc;
+      bs.tile_ne[i] = pn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) {
+      carry_c = pc + c;
+      carry_n = pn + n;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *v.n_pb = carry_n;
+}
+
+__device__ __forceinline__ int scene_of_key(const BinScratch& bs, uint32_t key) {
+  int lo = 0, hi = bs.n_scene_tab - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (bs.scene_tab[2 * mid] <= key)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return (int)bs.scene_tab[2 * lo + 1];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScratch bs) {
+  const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kPerThread;
+  uint32_t c[kPerThread];
+  uint32_t tc = 0, tn = 0;
+#pragma unroll
+  for (int q = 0; q < kPerThread; ++q) {
+    uint32_t k = base + q;
+    c[q] = k < v.n_keys ? v.cnt_cur[k] : 0u;
+    tc += c[q];
+    tn += c[q] ? 1u : 0u;
+  }
+  // block-wide exclusive scan of (tc, tn)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t ic = tc, in = tn;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t yc = __shfl_up_sync(0xffffffffu, ic, o);
+    uint32_t yn = __shfl_up_sync(0xffffffffu, in, o);
+    if (lane >= o) {
+      ic += yc;
+      in += yn;
+    }
+  }
+  __shared__ uint32_t wc[kScanThreads / 32], wn[kScanThreads / 32];
+  if (lane == 31) {
+    wc[warp] = ic;
+    wn[warp] = in;
+  }
+  __syncthreads();
+  uint32_t pc = bs.tile_cnt[blockIdx.x], pn = bs.tile_ne[blockIdx.x];
+  for (int w = 0; w < warp; ++w) {
+    pc += wc[w];
+    pn += wn[w];
+  }
+  pc += ic - tc;
+  pn += in - tn;
+#pragma unroll
+  for (int q = 0; q < kPerThread; ++q) {
+    uint32_t k = base + q;
+    if (k >= v.n_keys) break;
+    v.offset[k] = pc;
+    v.cursor[k] = pc;
+    v.cnt_nxt[k] = 0u;
+    if (c[q]) {
+      int sl = scene_of_key(bs, k);
+      v.pb_key[pn] = k;
+      v.pb_scene[pn] = (uint32_t)sl;
+      const SceneDev& s = v.scenes[sl];
+      int lb = (int)(k - s.key_base);
+      int bx = lb % s.npb, by = (lb / s.npb) % s.npb, bz = lb / (s.npb * s.npb);
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx)
+            v.gflag[s.grid_base + ((long long)(bz + dz) * s.nb + (by + dy)) * s.nb + (bx + dx)] = (uint32_t)sl + 1u;
+      pn += 1;
+    }
+    pc += c[q];
+  }
+}
+
+__global__ void k_scatter(StepView v) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n_cur; j += gridDim.x * blockDim.x) {
+    uint32_t key = v.key_cur[j];
+    if (key == CK_DEAD_KEY) continue;
+    uint32_t pos = warp_aggregated_inc(v.cursor, key);
+    v.perm[pos] = j;
+  }
+}
+
+__global__ void k_glist(StepView v, uint32_t n_gblocks) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_gblocks; g += gridDim.x * blockDim.x) {
+    uint32_t f = v.gflag[g];
+    if (f) {
+      uint32_t idx = warp_aggregated_inc(v.n_g, 0u);
+      v.g_list[idx] = g;
+      v.g_scene[idx] = f - 1u;
+      v.gflag[g] = 0u;
+    }
+  }
+}
+
+void launch_bin(cudaStream_t st, const StepView& v, const BinScratch& bs, int which, uint32_t n_gblocks,
+                int grid_ctas) {
+  uint32_t ntiles = (v.n_keys + kScanTile - 1) / kScanTile;
+  if (ntiles == 0) ntiles = 1;
+  switch (which) {
+    case LB_SCAN_TILES: k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(v, bs); break;
+    case LB_SCAN_TOP: k_scan_top<<<1, 1024, 0, st>>>(v, bs, ntiles); break;
+    case LB_SCAN_FINAL: k_scan_final<<<ntiles, kScanThreads, 0, st>>>(v, bs); break;
+    case LB_SCATTER: k_scatter<<<grid_ctas, 256, 0, st>>>(v); break;
+    case LB_GLIST: k_glist<<<grid_ctas, 256, 0, st>>>(v, n_gblocks); break;
+  }
+}
+
+}  // namespace ck

@@ -1,0 +1,921 @@
+// Host runtime and C ABI of the CK-MPM library: contexts, scene admission,
+// the per-step launch sequence, readback/upload and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ckmpm.h"
+#include "common.cuh"
+#include "launch.h"
+
+namespace {
+
+using ck::MatDev;
+using ck::Pool;
+using ck::SceneDev;
+
+struct Range {
+  int64_t start, len;
+};
+
+// First-fit allocator over an integer range.
+struct RangeAlloc {
+  std::vector<Range> free_;
+  int64_t cap = 0, high = 0;
+  void init(int64_t c) {
+    cap = c;
+    high = 0;
+    free_.clear();
+    if (c > 0) free_.push_back({0, c});
+  }
+  int64_t take(int64_t len) {
+    for (size_t i = 0; i < free_.size(); ++i) {
+      if (free_[i].len >= len) {
+        int64_t s = free_[i].start;
+        free_[i].start += len;
+        free_[i].len -= len;
+        if (free_[i].len == 0) free_.erase(free_.begin() + i);
+        high = std::max(high, s + len);
+        return s;
+      }
+    }
+    return -1;
+  }
+  void give(int64_t s, int64_t len) {
+    free_.push_back({s, len});
+    std::sort(free_.begin(), free_.end(), [](const Range& a, const Range& b) { return a.start < b.start; });
+    std::vector<Range> m;
+    for (auto& r : free_) {
+      if (!m.empty() && m.back().start + m.back().len == r.start)
+        m.back().len += r.len;
+      else
+        m.push_back(r);
+    }
+    free_.swap(m);
+  }
+};
+
+struct SceneHost {
+  bool used = false, alive = false;
+  int64_t n = 0;
+  int64_t key_base = 0, nkeys = 0;
+  int64_t grid_base = 0, ngb = 0;
+  int64_t mat_base = 0, nmat = 0;
+  int res = 0;
+};
+
+struct Seg {
+  int slot;
+  int64_t start, n;
+};
+
+struct PendingFree {
+  int slot;
+};
+
+}  // namespace
+
+struct ckmpm_ctx {
+  int kind = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ckmpm_allocator alloc{};
+  bool has_alloc = false;
+  int device = 0, sm_count = 1;
+  ck::LaunchCfg lc{};
+
+  int64_t cap_n = 0, cap_keys = 0, cap_gblocks = 0;
+  int cap_scenes = 0, cap_mats = 0;
+  bool per_E = false;
+
+  Pool pool[2]{};
+  int cur = 0;
+  uint32_t* key[2]{};
+  uint32_t* cnt[2]{};
+  uint32_t *offset = nullptr, *cursor = nullptr, *perm = nullptr, *pb_key = nullptr, *pb_scene = nullptr;
+  uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit)
+  uint32_t *gflag = nullptr, *g_list = nullptr, *g_scene = nullptr;
+  uint32_t *tile_cnt = nullptr, *tile_ne = nullptr, *scene_tab = nullptr;
+  float4 *Gacc = nullptr, *Gvel = nullptr;
+  SceneDev* d_scenes = nullptr;
+  MatDev* d_mats = nullptr;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+
+  std::vector<SceneHost> scenes;
+  std::vector<SceneDev> h_scenes;
+  std::vector<MatDev> h_mats;
+  RangeAlloc keys_alloc, grid_alloc, mat_alloc;
+  std::vector<int> pending_free;
+  int64_t n_cur = 0;
+  std::vector<Seg> layout;
+  bool keys_dirty = false, grids_dirty = false;
+  ckmpm_status sticky = CKMPM_OK;
+  int64_t steps = 0;
+  std::string msg;
+  std::vector<std::pair<void*, size_t>> allocs;
+
+  bool timing = false;
+  struct EvPair {
+    cudaEvent_t a, b;
+    int which;
+  };
+  std::vector<EvPair> ev_used, ev_free;
+  double ms_sum[8] = {0};
+  int64_t ms_cnt[8] = {0};
+  cudaEvent_t step_a = nullptr, step_b = nullptr;
+  double ms_last_step = 0;
+};
+
+namespace {
+
+ckmpm_status fail(ckmpm_ctx* c, ckmpm_status s, const std::string& m) {
+  if (c) c->msg = m;
+  return s;
+}
+
+ckmpm_status cuda_fail(ckmpm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, CKMPM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK_TRY(expr, where)                                   \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);  \
+  } while (0)
+
+void* dev_alloc(ckmpm_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (ctx->has_alloc) {
+    p = ctx->alloc.alloc(bytes, ctx->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) ctx->allocs.push_back({p, bytes});
+  return p;
+}
+
+void dev_free(ckmpm_ctx* ctx, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < ctx->allocs.size(); ++i) {
+    if (ctx->allocs[i].first == p) {
+      size_t b = ctx->allocs[i].second;
+      ctx->allocs.erase(ctx->allocs.begin() + i);
+      if (ctx->has_alloc)
+        ctx->alloc.free(p, b, ctx->alloc.user);
+      else
+        cudaFree(p);
+      return;
+    }
+  }
+}
+
+template <typename T>
+bool alloc_n(ckmpm_ctx* ctx, T*& p, int64_t n) {
+  p = (T*)dev_alloc(ctx, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  return p != nullptr;
+}
+
+bool alloc_pool(ckmpm_ctx* ctx, Pool& P, int64_t n) {
+  P.E = nullptr;
+  bool ok = alloc_n(ctx, P.X, n) && alloc_n(ctx, P.VM0, n) && alloc_n(ctx, P.VM1, n) && alloc_n(ctx, P.VM2, n) &&
+            alloc_n(ctx, P.F0, n) && alloc_n(ctx, P.F1, n) && alloc_n(ctx, P.F2, n) && alloc_n(ctx, P.ID, n);
+  if (ok && ctx->per_E) ok = alloc_n(ctx, P.E, n);
+  return ok;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+ck::StepView make_view(ckmpm_ctx* ctx) {
+  ck::StepView v{};
+  v.cur = ctx->pool[ctx->cur];
+  v.nxt = ctx->pool[ctx->cur ^ 1];
+  v.key_cur = ctx->key[ctx->cur];
+  v.key_nxt = ctx->key[ctx->cur ^ 1];
+  v.cnt_cur = ctx->cnt[ctx->cur];
+  v.cnt_nxt = ctx->cnt[ctx->cur ^ 1];
+  v.offset = ctx->offset;
+  v.cursor = ctx->cursor;
+  v.perm = ctx->perm;
+  v.pb_key = ctx->pb_key;
+  v.pb_scene = ctx->pb_scene;
+  v.n_pb = ctx->counters + 0;
+  v.n_g = ctx->counters + 1;
+  v.err = ctx->counters + 2;
+  v.fp64_count = (unsigned long long*)(ctx->counters + 4);
+  v.gflag = ctx->gflag;
+  v.g_list = ctx->g_list;
+  v.g_scene = ctx->g_scene;
+  v.Gacc = ctx->Gacc;
+  v.Gvel = ctx->Gvel;
+  v.scenes = ctx->d_scenes;
+  v.mats = ctx->d_mats;
+  v.n_keys = (uint32_t)std::max<int64_t>(ctx->keys_alloc.high, 1);
+  v.n_cur = (uint32_t)ctx->n_cur;
+  v.keep_gacc = 0;
+  return v;
+}
+
+ck::BinScratch make_bs(ckmpm_ctx* ctx, int n_tab) {
+  ck::BinScratch bs{};
+  bs.tile_cnt = ctx->tile_cnt;
+  bs.tile_ne = ctx->tile_ne;
+  bs.scene_tab = ctx->scene_tab;
+  bs.n_scene_tab = n_tab;
+  return bs;
+}
+
+// timing helpers
+void tbeg(ckmpm_ctx* ctx, ckmpm_ctx::EvPair& ep, int which) {
+  if (!ctx->timing) return;
+  if (ctx->ev_free.empty()) {
+    ckmpm_ctx::EvPair e{};
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+    ctx->ev_free.push_back(e);
+  }
+  ep = ctx->ev_free.back();
+  ctx->ev_free.pop_back();
+  ep.which = which;
+  cudaEventRecord(ep.a, ctx->stream);
+}
+void tend(ckmpm_ctx* ctx, ckmpm_ctx::EvPair& ep) {
+  if (!ctx->timing) return;
+  cudaEventRecord(ep.b, ctx->stream);
+  ctx->ev_used.push_back(ep);
+}
+void harvest_timing(ckmpm_ctx* ctx) {
+  for (auto& e : ctx->ev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      ctx->ms_sum[e.which] += ms;
+      ctx->ms_cnt[e.which] += 1;
+    }
+    ctx->ev_free.push_back(e);
+  }
+  ctx->ev_used.clear();
+  cudaGetLastError();
+}
+
+int upload_scene_tab(ckmpm_ctx* ctx) {
+  std::vector<uint32_t> tab;
+  std::vector<std::pair<int64_t, int>> al;
+  for (int s = 0; s < (int)ctx->scenes.size(); ++s)
+    if (ctx->scenes[s].alive) al.push_back({ctx->scenes[s].key_base, s});
+  std::sort(al.begin(), al.end());
+  for (auto& a : al) {
+    tab.push_back((uint32_t)a.first);
+    tab.push_back((uint32_t)a.second);
+  }
+  if (tab.empty()) {
+    tab.push_back(0);
+    tab.push_back(0);
+  }
+  cudaMemcpyAsync(ctx->scene_tab, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream);
+  return (int)(tab.size() / 2);
+}
+
+int n_scene_tab(ckmpm_ctx* ctx) {
+  int n = 0;
+  for (auto& s : ctx->scenes) n += s.alive ? 1 : 0;
+  return std::max(n, 1);
+}
+
+void process_pending(ckmpm_ctx* ctx) {
+  for (int slot : ctx->pending_free) {
+    SceneHost& s = ctx->scenes[slot];
+    ctx->keys_alloc.give(s.key_base, s.nkeys);
+    ctx->grid_alloc.give(s.grid_base, s.ngb);
+    ctx->mat_alloc.give(s.mat_base, s.nmat);
+    s = SceneHost{};
+  }
+  ctx->pending_free.clear();
+}
+
+void rebuild_layout_sorted(ckmpm_ctx* ctx) {
+  std::vector<std::pair<int64_t, int>> al;
+  for (int s = 0; s < (int)ctx->scenes.size(); ++s)
+    if (ctx->scenes[s].alive) al.push_back({ctx->scenes[s].key_base, s});
+  std::sort(al.begin(), al.end());
+  ctx->layout.clear();
+  int64_t start = 0;
+  for (auto& a : al) {
+    ctx->layout.push_back({a.second, start, ctx->scenes[a.second].n});
+    start += ctx->scenes[a.second].n;
+  }
+}
+
+const Seg* find_seg(ckmpm_ctx* ctx, int slot) {
+  for (auto& s : ctx->layout)
+    if (s.slot == slot) return &s;
+  return nullptr;
+}
+
+ckmpm_status read_device_error(ckmpm_ctx* ctx) {
+  uint32_t e = 0;
+  cudaError_t ce = cudaMemcpy(&e, ctx->counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "reading the device status word");
+  if (ctx->sticky == CKMPM_OK) {
+    if (e & CK_ERR_NONFINITE) {
+      ctx->sticky = CKMPM_ENONFINITE;
+      ctx->msg = "a non-finite particle state was produced";
+    } else if (e & CK_ERR_DOMAIN) {
+      ctx->sticky = CKMPM_EDOMAIN;
+      ctx->msg = "a particle left the valid interior [0.5 dx, (res-0.5) dx) and was clamped";
+    } else if (e & CK_ERR_INTERNAL) {
+      ctx->sticky = CKMPM_EINVAL;
+      ctx->msg = "internal consistency check failed (particle outside its block)";
+    } else if (e & CK_ERR_TIMEOUT) {
+      ctx->sticky = CKMPM_ETIMEOUT;
+      ctx->msg = "a bounded device wait gave up";
+    }
+  }
+  return ctx->sticky;
+}
+
+bool ensure_staging(ckmpm_ctx* ctx, size_t bytes) {
+  if (ctx->staging_bytes >= bytes) return true;
+  if (ctx->staging) {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, ctx->staging);
+    ctx->staging = nullptr;
+    ctx->staging_bytes = 0;
+  }
+  size_t b = std::max<size_t>(bytes, 1 << 20);
+  ctx->staging = dev_alloc(ctx, b);
+  if (!ctx->staging) return false;
+  ctx->staging_bytes = b;
+  return true;
+}
+
+ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
+  if (!s) return fail(ctx, CKMPM_EINVAL, "scene is NULL");
+  if (s->n < 1 || s->n > 0x7fffffffLL) return fail(ctx, CKMPM_EINVAL, "scene.n must be in [1, 2^31)");
+  if (!s->x) return fail(ctx, CKMPM_EINVAL, "scene.x is NULL");
+  if (s->res < 4 || s->res > 4096) return fail(ctx, CKMPM_EINVAL, "scene.res must be in [4, 4096]");
+  if (!(s->dx > 0) || !(s->dt > 0)) return fail(ctx, CKMPM_EINVAL, "scene.dx and scene.dt must be positive");
+  if (s->ppc < 1) return fail(ctx, CKMPM_EINVAL, "scene.ppc must be >= 1");
+  if (!s->materials || s->n_materials < 1 || s->n_materials > 255)
+    return fail(ctx, CKMPM_EINVAL, "scene needs 1..255 materials");
+  for (int i = 0; i < s->n_materials; ++i) {
+    const ckmpm_material& m = s->materials[i];
+    if (m.model != 0 && m.model != 1) return fail(ctx, CKMPM_EINVAL, "material.model must be 0 or 1");
+    if (!(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0))
+      return fail(ctx, CKMPM_EINVAL, "material needs E >= 0, -1 < nu < 0.5, rho > 0");
+  }
+  if (!(s->bc_cells >= 0)) return fail(ctx, CKMPM_EINVAL, "scene.bc_cells must be >= 0");
+  return CKMPM_OK;
+}
+
+ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
+  ctx->kind = cfg->kernel;
+  if (ctx->kind != 0 && ctx->kind != 1) return fail(ctx, CKMPM_EINVAL, "kernel must be 0 (CK) or 1 (quadratic)");
+  if (cfg->max_particles < 1 || cfg->max_keys < 1 || cfg->max_grid_blocks < 1 || cfg->max_scenes < 1 ||
+      cfg->max_scenes > 1024 || cfg->max_materials < 1 || cfg->max_materials > 65535)
+    return fail(ctx, CKMPM_EINVAL, "invalid capacities");
+  if (cfg->max_particles > 0x7fffffffLL || cfg->max_keys > 0x7fffffffLL || cfg->max_grid_blocks > 0x7fffffffLL)
+    return fail(ctx, CKMPM_EINVAL, "capacities must be below 2^31");
+  if (cfg->allocator) {
+    if (!cfg->allocator->alloc || !cfg->allocator->free) return fail(ctx, CKMPM_EINVAL, "allocator needs alloc and free");
+    ctx->alloc = *cfg->allocator;
+    ctx->has_alloc = true;
+  }
+  CK_TRY(cudaGetDevice(&ctx->device), "cudaGetDevice");
+  CK_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device), "device attributes");
+  int per_sm = 8;
+  if (const char* e = getenv("CKMPM_CTAS_PER_SM")) per_sm = std::max(1, atoi(e));
+  ctx->lc.persistent_ctas = ctx->sm_count * per_sm;
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    CK_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    ctx->own_stream = true;
+  }
+  ctx->lc.stream = ctx->stream;
+  ctx->cap_n = cfg->max_particles;
+  ctx->cap_keys = cfg->max_keys;
+  ctx->cap_gblocks = cfg->max_grid_blocks;
+  ctx->cap_scenes = cfg->max_scenes;
+  ctx->cap_mats = cfg->max_materials;
+  ctx->per_E = cfg->per_particle_E != 0;
+  const int NG = ctx->kind == 0 ? 2 : 1;
+  bool ok = alloc_pool(ctx, ctx->pool[0], ctx->cap_n) && alloc_pool(ctx, ctx->pool[1], ctx->cap_n) &&
+            alloc_n(ctx, ctx->key[0], ctx->cap_n) && alloc_n(ctx, ctx->key[1], ctx->cap_n) &&
+            alloc_n(ctx, ctx->perm, ctx->cap_n) && alloc_n(ctx, ctx->cnt[0], ctx->cap_keys) &&
+            alloc_n(ctx, ctx->cnt[1], ctx->cap_keys) && alloc_n(ctx, ctx->offset, ctx->cap_keys) &&
+            alloc_n(ctx, ctx->cursor, ctx->cap_keys) && alloc_n(ctx, ctx->pb_key, ctx->cap_keys) &&
+            alloc_n(ctx, ctx->pb_scene, ctx->cap_keys) && alloc_n(ctx, ctx->counters, 8) &&
+            alloc_n(ctx, ctx->gflag, ctx->cap_gblocks) && alloc_n(ctx, ctx->g_list, ctx->cap_gblocks) &&
+            alloc_n(ctx, ctx->g_scene, ctx->cap_gblocks) &&
+            alloc_n(ctx, ctx->tile_cnt, ceil_div(ctx->cap_keys, ck::kScanTile) + 1) &&
+            alloc_n(ctx, ctx->tile_ne, ceil_div(ctx->cap_keys, ck::kScanTile) + 1) &&
+            alloc_n(ctx, ctx->scene_tab, 2 * (int64_t)ctx->cap_scenes + 2) &&
+            alloc_n(ctx, ctx->Gacc, ctx->cap_gblocks * NG * ck::kBlockNodes) &&
+            alloc_n(ctx, ctx->Gvel, ctx->cap_gblocks * NG * ck::kBlockNodes) &&
+            alloc_n(ctx, ctx->d_scenes, ctx->cap_scenes) && alloc_n(ctx, ctx->d_mats, ctx->cap_mats);
+  if (!ok) return fail(ctx, CKMPM_ENOMEM, "device memory allocation failed");
+  CK_TRY(cudaMemsetAsync(ctx->cnt[0], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->cnt[1], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->counters, 0, sizeof(uint32_t) * 8, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->gflag, 0, sizeof(uint32_t) * ctx->cap_gblocks, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->Gacc, 0, sizeof(float4) * ctx->cap_gblocks * NG * ck::kBlockNodes, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->Gvel, 0, sizeof(float4) * ctx->cap_gblocks * NG * ck::kBlockNodes, ctx->stream), "memset");
+  ctx->scenes.assign(ctx->cap_scenes, SceneHost{});
+  ctx->h_scenes.assign(ctx->cap_scenes, SceneDev{});
+  ctx->h_mats.assign(ctx->cap_mats, MatDev{});
+  ctx->keys_alloc.init(ctx->cap_keys);
+  ctx->grid_alloc.init(ctx->cap_gblocks);
+  ctx->mat_alloc.init(ctx->cap_mats);
+  CK_TRY(cudaEventCreate(&ctx->step_a), "event");
+  CK_TRY(cudaEventCreate(&ctx->step_b), "event");
+  CK_TRY(cudaGetLastError(), "init");
+  return CKMPM_OK;
+}
+
+void scene_dims(int res, int64_t& npb, int64_t& nb) {
+  npb = ceil_div(res, 4);
+  nb = npb + 1;
+}
+
+bool capturing(ckmpm_ctx* ctx) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(ctx->stream, &st);
+  return st != cudaStreamCaptureStatusNone;
+}
+
+ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
+  const int NG = ctx->kind == 0 ? 2 : 1;
+  (void)NG;
+  ck::StepView v = make_view(ctx);
+  ckmpm_ctx::EvPair ep{};
+  if (ctx->grids_dirty) {
+    ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_CLEAR);
+    ctx->grids_dirty = false;
+  }
+  if (ctx->keys_dirty) {
+    CK_TRY(cudaMemsetAsync(ctx->cnt[ctx->cur], 0, sizeof(uint32_t) * v.n_keys, ctx->stream), "memset");
+    if (ctx->n_cur > 0)
+      ck::launch_rekey(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur],
+                       ctx->d_scenes, ctx->d_mats, (uint32_t)ctx->n_cur, v.err);
+    ctx->keys_dirty = false;
+  }
+  int64_t n_live = 0;
+  for (auto& s : ctx->scenes) n_live += s.alive ? s.n : 0;
+  if (n_live == 0) {
+    if (!probe) {
+      ctx->n_cur = 0;
+      ctx->layout.clear();
+      ctx->steps++;
+      process_pending(ctx);
+    }
+    CK_TRY(cudaGetLastError(), "step launch");
+    return CKMPM_OK;
+  }
+  ck::BinScratch bs = make_bs(ctx, n_scene_tab(ctx));
+  const uint32_t ngb = (uint32_t)std::max<int64_t>(ctx->grid_alloc.high, 1);
+  const int grid_ctas = ctx->sm_count * 4;
+  if (ctx->timing && !probe) cudaEventRecord(ctx->step_a, ctx->stream);
+  tbeg(ctx, ep, 0);
+  ck::launch_bin(ctx->stream, v, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
+  ck::launch_bin(ctx->stream, v, bs, ck::LB_SCAN_TOP, ngb, grid_ctas);
+  ck::launch_bin(ctx->stream, v, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 1);
+  ck::launch_bin(ctx->stream, v, bs, ck::LB_SCATTER, ngb, grid_ctas);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 5);
+  ck::launch_bin(ctx->stream, v, bs, ck::LB_GLIST, ngb, grid_ctas);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 2);
+  ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_P2G);
+  tend(ctx, ep);
+  v.keep_gacc = probe ? 1u : 0u;
+  tbeg(ctx, ep, 3);
+  ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_UPDATE);
+  tend(ctx, ep);
+  if (probe) {
+    ctx->grids_dirty = true;
+    CK_TRY(cudaGetLastError(), "probe launch");
+    return CKMPM_OK;
+  }
+  tbeg(ctx, ep, 4);
+  ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_G2P);
+  tend(ctx, ep);
+  if (ctx->timing) cudaEventRecord(ctx->step_b, ctx->stream);
+  CK_TRY(cudaGetLastError(), "step launch");
+  ctx->cur ^= 1;
+  ctx->n_cur = n_live;
+  rebuild_layout_sorted(ctx);
+  ctx->steps++;
+  process_pending(ctx);
+  return CKMPM_OK;
+}
+
+ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
+  ckmpm_status st = validate_scene(ctx, sc);
+  if (st != CKMPM_OK) return st;
+  if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "admission is not allowed during stream capture");
+  int64_t npb, nb;
+  scene_dims(sc->res, npb, nb);
+  const int64_t nkeys = npb * npb * npb, ngb = nb * nb * nb;
+  if (ctx->n_cur + sc->n > ctx->cap_n) return fail(ctx, CKMPM_ENOMEM, "particle capacity exceeded");
+  int slot = -1;
+  for (int s = 0; s < ctx->cap_scenes; ++s)
+    if (!ctx->scenes[s].used) {
+      slot = s;
+      break;
+    }
+  if (slot < 0) return fail(ctx, CKMPM_ENOMEM, "no free scene slot");
+  int64_t kb = ctx->keys_alloc.take(nkeys);
+  if (kb < 0) return fail(ctx, CKMPM_ENOMEM, "key-space capacity exceeded");
+  int64_t gb = ctx->grid_alloc.take(ngb);
+  if (gb < 0) {
+    ctx->keys_alloc.give(kb, nkeys);
+    return fail(ctx, CKMPM_ENOMEM, "grid-arena capacity exceeded");
+  }
+  int64_t mb = ctx->mat_alloc.take(sc->n_materials);
+  if (mb < 0) {
+    ctx->keys_alloc.give(kb, nkeys);
+    ctx->grid_alloc.give(gb, ngb);
+    return fail(ctx, CKMPM_ENOMEM, "material-table capacity exceeded");
+  }
+  size_t bx = sizeof(float) * 3 * sc->n;
+  size_t need = sc->is_device ? 0 : (2 * bx + (size_t)sc->n + 64);
+  if (need && !ensure_staging(ctx, need)) {
+    ctx->keys_alloc.give(kb, nkeys);
+    ctx->grid_alloc.give(gb, ngb);
+    ctx->mat_alloc.give(mb, sc->n_materials);
+    return fail(ctx, CKMPM_ENOMEM, "staging allocation failed");
+  }
+  SceneHost& h = ctx->scenes[slot];
+  h.used = true;
+  h.alive = true;
+  h.n = sc->n;
+  h.key_base = kb;
+  h.nkeys = nkeys;
+  h.grid_base = gb;
+  h.ngb = ngb;
+  h.mat_base = mb;
+  h.nmat = sc->n_materials;
+  h.res = sc->res;
+  SceneDev& d = ctx->h_scenes[slot];
+  d.dx = (float)sc->dx;
+  d.inv_dx = (float)(1.0 / sc->dx);
+  d.dt = (float)sc->dt;
+  d.V0 = (float)(sc->dx * sc->dx * sc->dx / sc->ppc);
+  d.gx = (float)sc->gravity[0];
+  d.gy = (float)sc->gravity[1];
+  d.gz = (float)sc->gravity[2];
+  d.bc = (float)sc->bc_cells;
+  d.res = sc->res;
+  d.npb = (int)npb;
+  d.nb = (int)nb;
+  d.key_base = (uint32_t)kb;
+  d.grid_base = gb;
+  d.j_tol = (float)sc->fp64_j_tol;
+  d.cond_tol = (float)sc->fp64_cond_tol;
+  d.gap_tol = (float)sc->fp64_gap_tol;
+  d.alive = 1;
+  const double V0 = sc->dx * sc->dx * sc->dx / sc->ppc;
+  for (int i = 0; i < sc->n_materials; ++i) {
+    const ckmpm_material& m = sc->materials[i];
+    MatDev& md = ctx->h_mats[mb + i];
+    md.model = m.model;
+    md.scene = slot;
+    md.mu = (float)(m.E / (2.0 * (1.0 + m.nu)));
+    md.lam = (float)(m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu)));
+    md.mass = (float)(m.rho * V0);
+    double s = std::sin(m.friction_deg * M_PI / 180.0);
+    md.alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s));
+    md.E = (float)m.E;
+    md.nu = (float)m.nu;
+  }
+  CK_TRY(cudaMemcpyAsync(ctx->d_scenes + slot, &d, sizeof(SceneDev), cudaMemcpyHostToDevice, ctx->stream), "upload scene");
+  CK_TRY(cudaMemcpyAsync(ctx->d_mats + mb, &ctx->h_mats[mb], sizeof(MatDev) * sc->n_materials, cudaMemcpyHostToDevice,
+                         ctx->stream),
+         "upload materials");
+  upload_scene_tab(ctx);
+  const float* dx_ = sc->x;
+  const float* dv_ = sc->v;
+  const uint8_t* dm_ = sc->mat;
+  if (!sc->is_device) {
+    char* stg = (char*)ctx->staging;
+    CK_TRY(cudaMemcpyAsync(stg, sc->x, bx, cudaMemcpyHostToDevice, ctx->stream), "upload x");
+    dx_ = (const float*)stg;
+    if (sc->v) {
+      CK_TRY(cudaMemcpyAsync(stg + bx, sc->v, bx, cudaMemcpyHostToDevice, ctx->stream), "upload v");
+      dv_ = (const float*)(stg + bx);
+    }
+    if (sc->mat) {
+      CK_TRY(cudaMemcpyAsync(stg + 2 * bx, sc->mat, (size_t)sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload mat");
+      dm_ = (const uint8_t*)(stg + 2 * bx);
+    }
+  }
+  // per-particle E defaults to the material's E
+  float* dE = nullptr;
+  if (ctx->per_E) {
+    std::vector<float> Ehost;
+    // material E by index, filled on device via a temporary when materials mix is simple: upload E per particle
+    Ehost.resize((size_t)sc->n);
+    std::vector<uint8_t> mh;
+    if (sc->mat) {
+      mh.resize((size_t)sc->n);
+      if (sc->is_device)
+        CK_TRY(cudaMemcpy(mh.data(), sc->mat, (size_t)sc->n, cudaMemcpyDeviceToHost), "read mat");
+      else
+        std::memcpy(mh.data(), sc->mat, (size_t)sc->n);
+    }
+    for (int64_t i = 0; i < sc->n; ++i) Ehost[i] = (float)sc->materials[sc->mat ? mh[i] : 0].E;
+    dE = (float*)dev_alloc(ctx, sizeof(float) * (size_t)sc->n);
+    if (!dE) return fail(ctx, CKMPM_ENOMEM, "allocation failed");
+    CK_TRY(cudaMemcpyAsync(dE, Ehost.data(), sizeof(float) * sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload E");
+  }
+  ck::launch_admit(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur], ctx->d_scenes,
+                   slot, (uint32_t)mb, (uint32_t)sc->n_materials, (uint32_t)ctx->n_cur, (uint32_t)sc->n, dx_, dv_, dm_, dE,
+                   ctx->counters + 2);
+  CK_TRY(cudaGetLastError(), "admit launch");
+  if (dE) {
+    CK_TRY(cudaStreamSynchronize(ctx->stream), "sync");
+    dev_free(ctx, dE);
+  }
+  ctx->layout.push_back({slot, ctx->n_cur, sc->n});
+  ctx->n_cur += sc->n;
+  if (scene_id) *scene_id = slot;
+  return CKMPM_OK;
+}
+
+int64_t field_floats(int field) {
+  switch (field) {
+    case CKMPM_FIELD_X:
+    case CKMPM_FIELD_V:
+      return 3;
+    case CKMPM_FIELD_B:
+    case CKMPM_FIELD_C:
+    case CKMPM_FIELD_F:
+      return 9;
+    case CKMPM_FIELD_E:
+      return 1;
+    default:
+      return 0;
+  }
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+const char* ckmpm_version(void) { return "ckmpm 0.1 (sm_103a)"; }
+
+ckmpm_status ckmpm_create_server(const ckmpm_config* cfg, ckmpm_ctx** out) {
+  if (!out) return CKMPM_EINVAL;
+  *out = nullptr;
+  if (!cfg) return CKMPM_EINVAL;
+  ckmpm_ctx* ctx = new (std::nothrow) ckmpm_ctx();
+  if (!ctx) return CKMPM_ENOMEM;
+  ckmpm_status st = init_ctx(ctx, cfg);
+  if (st != CKMPM_OK) {
+    ckmpm_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_create(const ckmpm_scene* scene, int kernel, void* stream, ckmpm_ctx** out) {
+  if (!out) return CKMPM_EINVAL;
+  *out = nullptr;
+  ckmpm_status st = validate_scene(nullptr, scene);
+  if (st != CKMPM_OK) return st;
+  int64_t npb, nb;
+  scene_dims(scene->res, npb, nb);
+  ckmpm_config cfg{};
+  cfg.kernel = kernel;
+  cfg.max_particles = scene->n;
+  cfg.max_keys = npb * npb * npb;
+  cfg.max_grid_blocks = nb * nb * nb;
+  cfg.max_scenes = 1;
+  cfg.max_materials = scene->n_materials;
+  cfg.per_particle_E = 0;
+  cfg.stream = stream;
+  ckmpm_ctx* ctx = nullptr;
+  st = ckmpm_create_server(&cfg, &ctx);
+  if (st != CKMPM_OK) return st;
+  int sid = -1;
+  st = admit_impl(ctx, scene, &sid);
+  if (st != CKMPM_OK) {
+    ckmpm_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_admit(ckmpm_ctx* ctx, const ckmpm_scene* scene, int* scene_id) {
+  if (!ctx) return CKMPM_EINVAL;
+  return admit_impl(ctx, scene, scene_id);
+}
+
+ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (scene_id < 0 || scene_id >= ctx->cap_scenes || !ctx->scenes[scene_id].alive)
+    return fail(ctx, CKMPM_ENOTFOUND, "unknown scene id");
+  if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "release is not allowed during stream capture");
+  ctx->scenes[scene_id].alive = false;
+  ctx->h_scenes[scene_id].alive = 0;
+  CK_TRY(cudaMemcpyAsync(ctx->d_scenes + scene_id, &ctx->h_scenes[scene_id], sizeof(SceneDev), cudaMemcpyHostToDevice,
+                         ctx->stream),
+         "upload scene");
+  upload_scene_tab(ctx);
+  ctx->keys_dirty = true;
+  ctx->pending_free.push_back(scene_id);
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_step(ckmpm_ctx* ctx, int n) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (n < 0) return fail(ctx, CKMPM_EINVAL, "n must be >= 0");
+  if (ctx->sticky != CKMPM_OK) return ctx->sticky;
+  for (int i = 0; i < n; ++i) {
+    ckmpm_status st = run_step(ctx, false);
+    if (st != CKMPM_OK) return st;
+  }
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_probe_grids(ckmpm_ctx* ctx) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (ctx->sticky != CKMPM_OK) return ctx->sticky;
+  return run_step(ctx, true);
+}
+
+ckmpm_status ckmpm_sync(ckmpm_ctx* ctx) {
+  if (!ctx) return CKMPM_EINVAL;
+  CK_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  return read_device_error(ctx);
+}
+
+int64_t ckmpm_scene_particles(const ckmpm_ctx* ctx, int scene_id) {
+  if (!ctx || scene_id < 0 || scene_id >= ctx->cap_scenes || !ctx->scenes[scene_id].alive) return -1;
+  return ctx->scenes[scene_id].n;
+}
+
+ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, size_t bytes, int dst_is_device) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (scene_id < 0 || scene_id >= ctx->cap_scenes || !ctx->scenes[scene_id].alive)
+    return fail(ctx, CKMPM_ENOTFOUND, "unknown scene id");
+  if (!dst) return fail(ctx, CKMPM_EINVAL, "dst is NULL");
+  if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "readback is not allowed during stream capture");
+  const SceneHost& h = ctx->scenes[scene_id];
+  const int NG = ctx->kind == 0 ? 2 : 1;
+  size_t want = 0;
+  if (field >= CKMPM_FIELD_GRID_M && field <= CKMPM_FIELD_GRID_V) {
+    int64_t n = h.res + 1;
+    want = sizeof(float) * (size_t)(NG * n * n * n) * (field == CKMPM_FIELD_GRID_M ? 1 : 3);
+  } else {
+    int64_t f = field_floats(field);
+    if (f == 0) return fail(ctx, CKMPM_EINVAL, "unknown field");
+    if (field == CKMPM_FIELD_E && !ctx->per_E) return fail(ctx, CKMPM_EINVAL, "context has no per-particle E");
+    want = sizeof(float) * (size_t)(f * h.n);
+  }
+  if (bytes != want) return fail(ctx, CKMPM_EINVAL, "readback size mismatch: expected " + std::to_string(want));
+  float* out = (float*)dst;
+  void* tmp = nullptr;
+  if (!dst_is_device) {
+    tmp = dev_alloc(ctx, want);
+    if (!tmp) return fail(ctx, CKMPM_ENOMEM, "temporary allocation failed");
+    out = (float*)tmp;
+  }
+  if (field >= CKMPM_FIELD_GRID_M) {
+    int64_t n = h.res + 1;
+    ck::launch_read_grid(ctx->kind, ctx->stream, ctx->Gacc, ctx->Gvel, ctx->d_scenes, scene_id,
+                         field - CKMPM_FIELD_GRID_M, out, (long long)NG * n * n * n);
+  } else {
+    const Seg* sg = find_seg(ctx, scene_id);
+    if (!sg) {
+      if (tmp) dev_free(ctx, tmp);
+      return fail(ctx, CKMPM_EINVAL, "scene has no particles in the pool");
+    }
+    ck::launch_read_particles(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id,
+                              (uint32_t)sg->start, (uint32_t)sg->n, field, out);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(dst, tmp, want, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (tmp) dev_free(ctx, tmp);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "readback");
+  return read_device_error(ctx);
+}
+
+ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* src, size_t bytes, int src_is_device) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (scene_id < 0 || scene_id >= ctx->cap_scenes || !ctx->scenes[scene_id].alive)
+    return fail(ctx, CKMPM_ENOTFOUND, "unknown scene id");
+  if (!src) return fail(ctx, CKMPM_EINVAL, "src is NULL");
+  if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "upload is not allowed during stream capture");
+  if (!(field == CKMPM_FIELD_X || field == CKMPM_FIELD_V || field == CKMPM_FIELD_B || field == CKMPM_FIELD_F ||
+        field == CKMPM_FIELD_E))
+    return fail(ctx, CKMPM_EINVAL, "field cannot be uploaded");
+  if (field == CKMPM_FIELD_E && !ctx->per_E) return fail(ctx, CKMPM_EINVAL, "context has no per-particle E");
+  const SceneHost& h = ctx->scenes[scene_id];
+  size_t want = sizeof(float) * (size_t)(field_floats(field) * h.n);
+  if (bytes != want) return fail(ctx, CKMPM_EINVAL, "upload size mismatch: expected " + std::to_string(want));
+  const Seg* sg = find_seg(ctx, scene_id);
+  if (!sg) return fail(ctx, CKMPM_EINVAL, "scene has no particles in the pool");
+  const float* in = (const float*)src;
+  void* tmp = nullptr;
+  if (!src_is_device) {
+    tmp = dev_alloc(ctx, want);
+    if (!tmp) return fail(ctx, CKMPM_ENOMEM, "temporary allocation failed");
+    CK_TRY(cudaMemcpyAsync(tmp, src, want, cudaMemcpyHostToDevice, ctx->stream), "upload copy");
+    in = (const float*)tmp;
+  }
+  ck::launch_write_particles(ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id, (uint32_t)sg->start,
+                             (uint32_t)sg->n, field, in);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (tmp) dev_free(ctx, tmp);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+  if (field == CKMPM_FIELD_X) ctx->keys_dirty = true;
+  return read_device_error(ctx);
+}
+
+ckmpm_status ckmpm_get_stats(ckmpm_ctx* ctx, ckmpm_stats* out) {
+  if (!ctx || !out) return CKMPM_EINVAL;
+  CK_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  uint32_t c[8];
+  CK_TRY(cudaMemcpy(c, ctx->counters, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+  std::memset(out, 0, sizeof(*out));
+  out->n_particles = ctx->n_cur;
+  out->n_particle_blocks = c[0];
+  out->n_grid_blocks = c[1];
+  out->steps = ctx->steps;
+  unsigned long long f64 = 0;
+  std::memcpy(&f64, &c[4], sizeof(f64));
+  out->fp64_particles = (int64_t)f64;
+  harvest_timing(ctx);
+  if (ctx->timing) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->step_a, ctx->step_b) == cudaSuccess) ctx->ms_last_step = ms;
+    cudaGetLastError();
+  }
+  out->ms_last_step = ctx->ms_last_step;
+  for (int i = 0; i < 8; ++i) {
+    out->ms_kernel[i] = ctx->ms_cnt[i] ? ctx->ms_sum[i] / ctx->ms_cnt[i] : 0.0;
+    out->launches_kernel[i] = ctx->ms_cnt[i];
+  }
+  out->launches_per_step = 8;
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_set_timing(ckmpm_ctx* ctx, int on) {
+  if (!ctx) return CKMPM_EINVAL;
+  ctx->timing = on != 0;
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_reset_timing(ckmpm_ctx* ctx) {
+  if (!ctx) return CKMPM_EINVAL;
+  CK_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  harvest_timing(ctx);
+  for (int i = 0; i < 8; ++i) {
+    ctx->ms_sum[i] = 0;
+    ctx->ms_cnt[i] = 0;
+  }
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_destroy(ckmpm_ctx* ctx) {
+  if (!ctx) return CKMPM_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  harvest_timing(ctx);
+  for (auto& e : ctx->ev_free) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  if (ctx->step_a) cudaEventDestroy(ctx->step_a);
+  if (ctx->step_b) cudaEventDestroy(ctx->step_b);
+  while (!ctx->allocs.empty()) dev_free(ctx, ctx->allocs.back().first);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaGetLastError();
+  delete ctx;
+  return CKMPM_OK;
+}
+
+const char* ckmpm_last_error(const ckmpm_ctx* ctx) {
+  if (!ctx) return "no context";
+  return ctx->msg.empty() ? "no error" : ctx->msg.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// 3x3 singular value decomposition and the constitutive models, templated on
+// the floating-point type so the same code runs in float32 and float64.
+//
+// SVD method: one-sided Jacobi in the spirit of McAdams, Selle, Tamstorf,
+// Teran and Sifakis, "Computing the Singular Value Decomposition of 3x3
+// matrices with minimal branching and elementary floating point operations"
+// (UW-Madison TR1690, 2011): a symmetric cyclic Jacobi eigen-sweep on F^T F
+// gives V, then a Givens QR of F V gives U and the singular values.  The
+// Jacobi rotations here are the exact textbook ones (tan from the smaller root
+// of t^2 + 2 theta t - 1 = 0), not the paper's approximate quaternion Givens.
+// The result is rotation-variant: det U = det V = +1, sigma_0 >= sigma_1 >= 0
+// and sigma_2 carries the sign of det F.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ck {
+
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+  __device__ static __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  __device__ static __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+  __device__ static __forceinline__ float abs_(float x) { return fabsf(x); }
+  __device__ static __forceinline__ float log_(float x) { return logf(x); }
+  __device__ static __forceinline__ float exp_(float x) { return expf(x); }
+  __device__ static __forceinline__ float hypot_(float a, float b) { return hypotf(a, b); }
+  static constexpr int sweeps = 5;
+  static constexpr float huge_theta = 1e15f;
+};
+template <>
+struct Num<double> {
+  __device__ static __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  __device__ static __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+  __device__ static __forceinline__ double abs_(double x) { return fabs(x); }
+  __device__ static __forceinline__ double log_(double x) { return log(x); }
+  __device__ static __forceinline__ double exp_(double x) { return exp(x); }
+  __device__ static __forceinline__ double hypot_(double a, double b) { return hypot(a, b); }
+  static constexpr int sweeps = 8;
+  static constexpr double huge_theta = 1e150;
+};
+
+// Row-major 3x3 helpers.
+#define CK_M(a, i, j) (a)[(i)*3 + (j)]
+
+template <typename T>
+__device__ __forceinline__ void jacobi_rotate(T* S, T* V, int p, int q, int r) {
+  T apq = CK_M(S, p, q);
+  if (apq == T(0)) return;
+  T theta = (CK_M(S, q, q) - CK_M(S, p, p)) / (T(2) * apq);
+  T at = Num<T>::abs_(theta);
+  T t = at > Num<T>::huge_theta ? T(0.5) / theta
+                                : (theta >= T(0) ? T(1) : T(-1)) / (at + Num<T>::sqrt_(theta * theta + T(1)));
+  T c = Num<T>::rsqrt_(t * t + T(1));
+  T s = t * c;
+  T spp = CK_M(S, p, p) - t * apq;
+  T sqq = CK_M(S, q, q) + t * apq;
+  T srp = CK_M(S, r, p), srq = CK_M(S, r, q);
+  T nrp = c * srp - s * srq;
+  T nrq = s * srp + c * srq;
+  CK_M(S, p, p) = spp;
+  CK_M(S, q, q) = sqq;
+  CK_M(S, p, q) = T(0);
+  CK_M(S, q, p) = T(0);
+  CK_M(S, r, p) = nrp;
+  CK_M(S, p, r) = nrp;
+  CK_M(S, r, q) = nrq;
+  CK_M(S, q, r) = nrq;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T vp = CK_M(V, i, p), vq = CK_M(V, i, q);
+    CK_M(V, i, p) = c * vp - s * vq;
+    CK_M(V, i, q) = s * vp + c * vq;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void swap_cols_neg(T* V, T* e, int a, int b) {
+  // swap eigenpairs a and b; negate one column so det V stays +1
+  T t = e[a];
+  e[a] = e[b];
+  e[b] = t;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T va = CK_M(V, i, a);
+    CK_M(V, i, a) = CK_M(V, i, b);
+    CK_M(V, i, b) = -va;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void givens_rows(T* Bm, T* U, int p, int q) {
+  // zero Bm[q][p] by rotating rows p and q; accumulate U <- U G^T
+  T a = CK_M(Bm, p, p), b = CK_M(Bm, q, p);
+  T r = Num<T>::hypot_(a, b);
+  T c = T(1), s = T(0);
+  if (r > T(0)) {
+    c = a / r;
+    s = b / r;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    T bp = CK_M(Bm, p, j), bq = CK_M(Bm, q, j);
+    CK_M(Bm, p, j) = c * bp + s * bq;
+    CK_M(Bm, q, j) = -s * bp + c * bq;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T up = CK_M(U, i, p), uq = CK_M(U, i, q);
+    CK_M(U, i, p) = c * up + s * uq;
+    CK_M(U, i, q) = -s * up + c * uq;
+  }
+}
+
+// F = U diag(sig) V^T, rotation-variant.
+template <typename T>
+__device__ __forceinline__ void svd3(const T* F, T* U, T* sig, T* V) {
+  T S[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      CK_M(S, i, j) = CK_M(F, 0, i) * CK_M(F, 0, j) + CK_M(F, 1, i) * CK_M(F, 1, j) + CK_M(F, 2, i) * CK_M(F, 2, j);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? T(1) : T(0);
+#pragma unroll 1
+  for (int sw = 0; sw < Num<T>::sweeps; ++sw) {
+    jacobi_rotate(S, V, 0, 1, 2);
+    jacobi_rotate(S, V, 0, 2, 1);
+    jacobi_rotate(S, V, 1, 2, 0);
+  }
+  T e[3] = {CK_M(S, 0, 0), CK_M(S, 1, 1), CK_M(S, 2, 2)};
+  if (e[0] < e[1]) swap_cols_neg(V, e, 0, 1);
+  if (e[0] < e[2]) swap_cols_neg(V, e, 0, 2);
+  if (e[1] < e[2]) swap_cols_neg(V, e, 1, 2);
+  T Bm[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      CK_M(Bm, i, j) = CK_M(F, i, 0) * CK_M(V, 0, j) + CK_M(F, i, 1) * CK_M(V, 1, j) + CK_M(F, i, 2) * CK_M(V, 2, j);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) U[i] = (i % 4 == 0) ? T(1) : T(0);
+  givens_rows(Bm, U, 0, 1);
+  givens_rows(Bm, U, 0, 2);
+  givens_rows(Bm, U, 1, 2);
+  sig[0] = CK_M(Bm, 0, 0);
+  sig[1] = CK_M(Bm, 1, 1);
+  sig[2] = CK_M(Bm, 2, 2);
+}
+
+// ---------------------------------------------------------------- materials
+
+constexpr float kSigmaFloor = 1e-6f;
+
+// Fixed-corotated Kirchhoff stress tau = 2 mu (F - R) F^T + lam J (J - 1) I,
+// R = U V^T (stomakhin2012, cited in Sec. 6.1).
+template <typename T>
+__device__ __forceinline__ void fc_tau(const T* F, const T* U, const T* sig, const T* V, T mu, T lam, T* tau) {
+  T R[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      CK_M(R, i, j) = CK_M(U, i, 0) * CK_M(V, j, 0) + CK_M(U, i, 1) * CK_M(V, j, 1) + CK_M(U, i, 2) * CK_M(V, j, 2);
+  T J = sig[0] * sig[1] * sig[2];
+  T D[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) D[i] = F[i] - R[i];
+  T vol = lam * J * (J - T(1));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      CK_M(tau, i, j) = T(2) * mu * (CK_M(D, i, 0) * CK_M(F, j, 0) + CK_M(D, i, 1) * CK_M(F, j, 1) + CK_M(D, i, 2) * CK_M(F, j, 2)) +
+                        (i == j ? vol : T(0));
+}
+
+// Hencky Kirchhoff stress U diag(2 mu eps + lam tr eps) U^T, eps = ln sigma.
+template <typename T>
+__device__ __forceinline__ void hencky_tau(const T* U, const T* sig, T mu, T lam, T* tau) {
+  T e0 = Num<T>::log_(sig[0] > T(kSigmaFloor) ? sig[0] : T(kSigmaFloor));
+  T e1 = Num<T>::log_(sig[1] > T(kSigmaFloor) ? sig[1] : T(kSigmaFloor));
+  T e2 = Num<T>::log_(sig[2] > T(kSigmaFloor) ? sig[2] : T(kSigmaFloor));
+  T tr = e0 + e1 + e2;
+  T d0 = T(2) * mu * e0 + lam * tr, d1 = T(2) * mu * e1 + lam * tr, d2 = T(2) * mu * e2 + lam * tr;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      CK_M(tau, i, j) = CK_M(U, i, 0) * d0 * CK_M(U, j, 0) + CK_M(U, i, 1) * d1 * CK_M(U, j, 1) + CK_M(U, i, 2) * d2 * CK_M(U, j, 2);
+}
+
+// Drucker-Prager projection of the singular values (klar2016): returns true
+// when sigma changed.  Tension or a purely volumetric state goes to the tip.
+template <typename T>
+__device__ __forceinline__ bool dp_project(T* sig, T mu, T lam, T alpha) {
+  T e0 = Num<T>::log_(sig[0] > T(kSigmaFloor) ? sig[0] : T(kSigmaFloor));
+  T e1 = Num<T>::log_(sig[1] > T(kSigmaFloor) ? sig[1] : T(kSigmaFloor));
+  T e2 = Num<T>::log_(sig[2] > T(kSigmaFloor) ? sig[2] : T(kSigmaFloor));
+  T tr = e0 + e1 + e2;
+  T h0 = e0 - tr / T(3), h1 = e1 - tr / T(3), h2 = e2 - tr / T(3);
+  T nrm = Num<T>::sqrt_(h0 * h0 + h1 * h1 + h2 * h2);
+  if (tr >= T(0) || nrm <= T(0)) {
+    sig[0] = sig[1] = sig[2] = T(1);
+    return true;
+  }
+  T dg = nrm + (T(3) * lam + T(2) * mu) / (T(2) * mu) * tr * alpha;
+  if (dg <= T(0)) return false;
+  T k = dg / nrm;
+  sig[0] = Num<T>::exp_(e0 - k * h0);
+  sig[1] = Num<T>::exp_(e1 - k * h1);
+  sig[2] = Num<T>::exp_(e2 - k * h2);
+  return true;
+}
+
+// U diag(sig) V^T
+template <typename T>
+__device__ __forceinline__ void usvt(const T* U, const T* sig, const T* V, T* F) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      CK_M(F, i, j) = CK_M(U, i, 0) * sig[0] * CK_M(V, j, 0) + CK_M(U, i, 1) * sig[1] * CK_M(V, j, 1) +
+                      CK_M(U, i, 2) * sig[2] * CK_M(V, j, 2);
+}
+
+// Constitutive update on F (already advanced by (I + dt C)): plasticity for
+// Drucker-Prager, then the Kirchhoff stress of the resulting F.
+template <typename T>
+__device__ __forceinline__ void constitutive(int model, T* F, T mu, T lam, T alpha, T* tau, T* sig_out) {
+  T U[9], V[9], sig[3];
+  svd3<T>(F, U, sig, V);
+  if (model == 1) {
+    if (dp_project<T>(sig, mu, lam, alpha)) usvt<T>(U, sig, V, F);
+    hencky_tau<T>(U, sig, mu, lam, tau);
+  } else {
+    fc_tau<T>(F, U, sig, V, mu, lam, tau);
+  }
+  sig_out[0] = sig[0];
+  sig_out[1] = sig[1];
+  sig_out[2] = sig[2];
+}
+
+// Kirchhoff stress of a given F without plasticity (used by readback/upload).
+template <typename T>
+__device__ __forceinline__ void stress_only(int model, const T* F, T mu, T lam, T* tau) {
+  T U[9], V[9], sig[3];
+  svd3<T>(F, U, sig, V);
+  if (model == 1)
+    hencky_tau<T>(U, sig, mu, lam, tau);
+  else
+    fc_tau<T>(F, U, sig, V, mu, lam, tau);
+}
+
+}  // namespace ck

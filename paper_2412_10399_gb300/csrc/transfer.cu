@@ -1,0 +1,780 @@
+// P2G, grid update and fused G2P + constitutive kernels of the CK-MPM step,
+// for the compact kernel on the dual grid (KIND 0) and the quadratic
+// B-spline comparison path (KIND 1).
+//
+// One CTA works on one particle block (4x4x4 cells of the reference grid G-,
+// Sec. 5.1) at a time and loops over the block list (persistent grid-stride
+// launch over all resident scenes).  The nodes that the block's particles can
+// touch are staged in shared memory:
+//   CK:  G- nodes [4P, 4P+4]^3 (125) and G+ nodes [4P, 4P+5]^3 (216) = 341
+//   quadratic: nodes [4P, 4P+5]^3 = 216
+// P2G accumulates there with shared-memory atomics and flushes each touched
+// node once with a 16-byte global atomic; G2P gathers from the staged copy.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "launch.h"
+#include "svd3.cuh"
+
+namespace ck {
+
+constexpr float kInv2Pi = 0.15915494309189535f;
+
+template <int KIND>
+struct Geo;
+template <>
+struct Geo<0> {
+  static constexpr int NG = 2;
+  static constexpr int E0 = 5, E1 = 6;
+  static constexpr int N0 = 125;
+  static constexpr int NS = 341;
+  static constexpr float half = 0.5f;
+};
+template <>
+struct Geo<1> {
+  static constexpr int NG = 1;
+  static constexpr int E0 = 6, E1 = 6;
+  static constexpr int N0 = 216;
+  static constexpr int NS = 216;
+  static constexpr float half = 1.0f;
+};
+
+// staged index -> (slot, local node coordinates)
+template <int KIND>
+__device__ __forceinline__ void staged_coords(int j, int& slot, int& lx, int& ly, int& lz) {
+  constexpr int E0 = Geo<KIND>::E0;
+  if (j < Geo<KIND>::N0) {
+    slot = 0;
+    lx = j % E0;
+    ly = (j / E0) % E0;
+    lz = j / (E0 * E0);
+  } else {
+    j -= Geo<KIND>::N0;
+    slot = 1;
+    lx = j % 6;
+    ly = (j / 6) % 6;
+    lz = j / 36;
+  }
+}
+
+// global arena index of node (ix, iy, iz) of a grid slot in scene s
+template <int KIND>
+__device__ __forceinline__ long long arena_index(const SceneDev& s, int slot, int ix, int iy, int iz) {
+  long long gb = s.grid_base + ((long long)(iz >> 2) * s.nb + (iy >> 2)) * s.nb + (ix >> 2);
+  int l = ((iz & 3) * 4 + (iy & 3)) * 4 + (ix & 3);
+  return (gb * Geo<KIND>::NG + slot) * kBlockNodes + l;
+}
+
+// ------------------------------------------------------------------ stencils
+
+// Weights, node offsets (x_i - x_p in cells) and D^-1 (cells^-2) of one
+// particle.  CK: K1 weights on both grids from one sine per axis
+// (sin 2 pi f- = -sin 2 pi f+), D = Lambda + s s^T with the closed form
+// Lambda_a = (m2(f+) + m2(f-))/2 - s_a^2, s_a = sin(2 pi f+_a)/(2 pi),
+// inverted by Sherman-Morrison.  Quadratic: B-spline weights, D^-1 = 4 I.
+template <int KIND>
+struct Sten;
+
+template <>
+struct Sten<0> {
+  int r[2][3];        // base node of each slot relative to the block origin
+  float w[2][3][2];   // per slot, axis, node
+  float d[2][3][2];
+  float Di[9];
+  __device__ __forceinline__ bool set(float ux, float uy, float uz, int ox, int oy, int oz) {
+    float u[3] = {ux, uy, uz};
+    int o[3] = {ox, oy, oz};
+    float s[3], lam[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cell<0> c;
+      c.set(u[a]);
+      r[0][a] = c.bm - o[a];
+      r[1][a] = c.bp - o[a];
+      ok = ok && (r[0][a] >= 0) && (r[0][a] <= 3) && (r[1][a] >= 0) && (r[1][a] <= 4);
+      float sg = sinpif(2.0f * c.fp) * kInv2Pi;
+      w[1][a][0] = 1.0f - c.fp + sg;
+      w[1][a][1] = c.fp - sg;
+      d[1][a][0] = -c.fp;
+      d[1][a][1] = 1.0f - c.fp;
+      w[0][a][0] = 1.0f - c.fm - sg;
+      w[0][a][1] = c.fm + sg;
+      d[0][a][0] = -c.fm;
+      d[0][a][1] = 1.0f - c.fm;
+      float m2p = c.fp * (1.0f - c.fp) - sg * (1.0f - 2.0f * c.fp);
+      float m2m = c.fm * (1.0f - c.fm) + sg * (1.0f - 2.0f * c.fm);
+      lam[a] = 0.5f * (m2p + m2m) - sg * sg;
+      s[a] = sg;
+    }
+    float li[3] = {1.0f / lam[0], 1.0f / lam[1], 1.0f / lam[2]};
+    float y[3] = {li[0] * s[0], li[1] * s[1], li[2] * s[2]};
+    float den = 1.0f / (1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Di[i * 3 + j] = (i == j ? li[i] : 0.0f) - y[i] * y[j] * den;
+    return ok;
+  }
+};
+
+template <>
+struct Sten<1> {
+  int r[3];
+  float w[3][3];
+  float d[3][3];
+  __device__ __forceinline__ bool set(float ux, float uy, float uz, int ox, int oy, int oz) {
+    float u[3] = {ux, uy, uz};
+    int o[3] = {ox, oy, oz};
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cell<1> c;
+      c.set(u[a]);
+      r[a] = c.b - o[a];
+      ok = ok && (r[a] >= 0) && (r[a] <= 3);
+      float f = c.f;
+      w[a][0] = 0.5f * (1.5f - f) * (1.5f - f);
+      w[a][1] = 0.75f - (f - 1.0f) * (f - 1.0f);
+      w[a][2] = 0.5f * (f - 0.5f) * (f - 0.5f);
+      d[a][0] = -f;
+      d[a][1] = 1.0f - f;
+      d[a][2] = 2.0f - f;
+    }
+    return ok;
+  }
+};
+
+// Visit every (node, weight, offset) of a stencil: fn(staged_index, w, dx, dy, dz).
+template <typename Fn>
+__device__ __forceinline__ void for_nodes(const Sten<0>& st, Fn&& fn) {
+#pragma unroll
+  for (int slot = 0; slot < 2; ++slot) {
+    const int E = slot == 0 ? 5 : 6;
+    const int base = slot == 0 ? 0 : 125;
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+      for (int sy = 0; sy < 2; ++sy) {
+        float wyz = st.w[slot][1][sy] * st.w[slot][2][sz];
+        int row = base + ((st.r[slot][2] + sz) * E + (st.r[slot][1] + sy)) * E + st.r[slot][0];
+#pragma unroll
+        for (int sx = 0; sx < 2; ++sx)
+          fn(row + sx, st.w[slot][0][sx] * wyz, st.d[slot][0][sx], st.d[slot][1][sy], st.d[slot][2][sz]);
+      }
+  }
+}
+
+template <typename Fn>
+__device__ __forceinline__ void for_nodes(const Sten<1>& st, Fn&& fn) {
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz)
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      float wyz = st.w[1][sy] * st.w[2][sz];
+      int row = ((st.r[2] + sz) * 6 + (st.r[1] + sy)) * 6 + st.r[0];
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx) fn(row + sx, st.w[0][sx] * wyz, st.d[0][sx], st.d[1][sy], st.d[2][sz]);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void dinv_of(const Sten<KIND>& st, float* Di);
+template <>
+__device__ __forceinline__ void dinv_of(const Sten<0>& st, float* Di) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Di[i] = st.Di[i];
+}
+template <>
+__device__ __forceinline__ void dinv_of(const Sten<1>& st, float* Di) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Di[i] = (i % 4 == 0) ? 4.0f : 0.0f;
+}
+
+__device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, int& ox, int& oy, int& oz) {
+  int lb = (int)(key - s.key_base);
+  int bx = lb % s.npb;
+  int by = (lb / s.npb) % s.npb;
+  int bz = lb / (s.npb * s.npb);
+  ox = bx * 4;
+  oy = by * 4;
+  oz = bz * 4;
+}
+
+// ------------------------------------------------------------------------ P2G
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_p2g(StepView v) {
+  constexpr int NS = Geo<KIND>::NS;
+  __shared__ float sm[4][NS];
+  const uint32_t npb = *v.n_pb;
+  for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
+    const uint32_t key = v.pb_key[bi];
+    const SceneDev s = v.scenes[v.pb_scene[bi]];
+    const uint32_t start = v.offset[key];
+    const uint32_t cnt = v.cnt_cur[key];
+    int ox, oy, oz;
+    decode_block(s, key, ox, oy, oz);
+    for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+      sm[0][j] = 0.f;
+      sm[1][j] = 0.f;
+      sm[2][j] = 0.f;
+      sm[3][j] = 0.f;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const uint32_t p = v.perm[start + i];
+      const float4 X = v.cur.X[p];
+      const float4 a = v.cur.VM0[p];
+      const float4 b = v.cur.VM1[p];
+      const float4 c = v.cur.VM2[p];
+      const MatDev mt = v.mats[__float_as_uint(X.w)];
+      Sten<KIND> st;
+      if (!st.set(X.x * s.inv_dx, X.y * s.inv_dx, X.z * s.inv_dx, ox, oy, oz)) {
+        flag_error(v.err, CK_ERR_INTERNAL);
+        continue;
+      }
+      float Di[9];
+      dinv_of<KIND>(st, Di);
+      const float M[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+      // A^ = M D^-1 / dx so that A (x_i - x_p) = A^ (offset in cells)
+      float A[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          A[r * 3 + q] = (M[r * 3 + 0] * Di[0 * 3 + q] + M[r * 3 + 1] * Di[1 * 3 + q] + M[r * 3 + 2] * Di[2 * 3 + q]) * s.inv_dx;
+      const float m = mt.mass;
+      const float px = m * a.x, py = m * a.y, pz = m * a.z;
+      for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
+        atomicAdd(&sm[0][j], w * m);
+        atomicAdd(&sm[1][j], w * (px + A[0] * dx + A[1] * dy + A[2] * dz));
+        atomicAdd(&sm[2][j], w * (py + A[3] * dx + A[4] * dy + A[5] * dz));
+        atomicAdd(&sm[3][j], w * (pz + A[6] * dx + A[7] * dy + A[8] * dz));
+      });
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+      float mm = sm[0][j];
+      if (mm != 0.f) {
+        int slot, lx, ly, lz;
+        staged_coords<KIND>(j, slot, lx, ly, lz);
+        long long gi = arena_index<KIND>(s, slot, ox + lx, oy + ly, oz + lz);
+        atomicAdd(&v.Gacc[gi], make_float4(mm, sm[1][j], sm[2][j], sm[3][j]));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- grid update
+
+// Sec. 4.3.3 per grid: v~ = (m v + dt f)/m + dt g on nodes with m > 0, zero
+// elsewhere; sticky walls zero v~ where a node coordinate (in cells, node i of
+// G- at i + 1/4, of G+ at i - 1/4, quadratic at i) is < bc or > res - bc.
+template <int KIND>
+__global__ void __launch_bounds__(128) k_grid_update(StepView v) {
+  constexpr int NG = Geo<KIND>::NG;
+  const uint32_t ng = *v.n_g;
+  for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+    const uint32_t g = v.g_list[gi];
+    const SceneDev s = v.scenes[v.g_scene[gi]];
+    long long lb = (long long)g - s.grid_base;
+    int gx = (int)(lb % s.nb), gy = (int)((lb / s.nb) % s.nb), gz = (int)(lb / ((long long)s.nb * s.nb));
+    for (int t = threadIdx.x; t < NG * kBlockNodes; t += blockDim.x) {
+      int slot = t / kBlockNodes, l = t % kBlockNodes;
+      int ix = gx * 4 + (l & 3), iy = gy * 4 + ((l >> 2) & 3), iz = gz * 4 + (l >> 4);
+      float off = KIND == 0 ? (slot == 0 ? 0.25f : -0.25f) : 0.0f;
+      long long idx = ((long long)g * NG + slot) * kBlockNodes + l;
+      float4 acc = v.Gacc[idx];
+      float4 o = make_float4(0.f, 0.f, 0.f, acc.x);
+      if (acc.x > 0.f) {
+        o.x = acc.y / acc.x + s.dt * s.gx;
+        o.y = acc.z / acc.x + s.dt * s.gy;
+        o.z = acc.w / acc.x + s.dt * s.gz;
+      }
+      float px = ix + off, py = iy + off, pz = iz + off;
+      float hi = (float)s.res - s.bc;
+      bool wall = px < s.bc || py < s.bc || pz < s.bc || px > hi || py > hi || pz > hi;
+      if (wall) o.x = o.y = o.z = 0.f;
+      v.Gvel[idx] = o;
+      if (!v.keep_gacc) v.Gacc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// ------------------------------------------------------ G2P + constitutive
+
+__device__ __forceinline__ float min3(float a, float b, float c) { return fminf(a, fminf(b, c)); }
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_g2p(StepView v) {
+  constexpr int NS = Geo<KIND>::NS;
+  __shared__ float sv[3][NS];
+  const uint32_t npb = *v.n_pb;
+  for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
+    const uint32_t key = v.pb_key[bi];
+    const SceneDev s = v.scenes[v.pb_scene[bi]];
+    const uint32_t start = v.offset[key];
+    const uint32_t cnt = v.cnt_cur[key];
+    int ox, oy, oz;
+    decode_block(s, key, ox, oy, oz);
+    for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+      int slot, lx, ly, lz;
+      staged_coords<KIND>(j, slot, lx, ly, lz);
+      float4 g = v.Gvel[arena_index<KIND>(s, slot, ox + lx, oy + ly, oz + lz)];
+      sv[0][j] = g.x;
+      sv[1][j] = g.y;
+      sv[2][j] = g.z;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const uint32_t t = start + i;
+      const uint32_t p = v.perm[t];
+      const float4 X = v.cur.X[p];
+      const float4 f0 = v.cur.F0[p];
+      const float4 f1 = v.cur.F1[p];
+      const float f2 = v.cur.F2[p];
+      const uint32_t id = v.cur.ID[p];
+      const uint32_t mi = __float_as_uint(X.w);
+      const MatDev mt = v.mats[mi];
+      float mu = mt.mu, lam = mt.lam;
+      float Ep = 0.f;
+      if (v.cur.E) {
+        Ep = v.cur.E[p];
+        mu = Ep / (2.0f * (1.0f + mt.nu));
+        lam = Ep * mt.nu / ((1.0f + mt.nu) * (1.0f - 2.0f * mt.nu));
+      }
+      Sten<KIND> st;
+      if (!st.set(X.x * s.inv_dx, X.y * s.inv_dx, X.z * s.inv_dx, ox, oy, oz)) {
+        flag_error(v.err, CK_ERR_INTERNAL);
+        continue;
+      }
+      float vx = 0.f, vy = 0.f, vz = 0.f;
+      float Bh[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Bh[q] = 0.f;
+      for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
+        float gx = sv[0][j] * w, gy = sv[1][j] * w, gz = sv[2][j] * w;
+        vx += gx;
+        vy += gy;
+        vz += gz;
+        Bh[0] += gx * dx; Bh[1] += gx * dy; Bh[2] += gx * dz;
+        Bh[3] += gy * dx; Bh[4] += gy * dy; Bh[5] += gy * dz;
+        Bh[6] += gz * dx; Bh[7] += gz * dy; Bh[8] += gz * dz;
+      });
+      const float h = Geo<KIND>::half;
+      vx *= h;
+      vy *= h;
+      vz *= h;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Bh[q] *= h;
+      float Di[9];
+      dinv_of<KIND>(st, Di);
+      // C = B D^-1 = Bh Di / dx ; F' = (I + dt C) F
+      float G[9];
+      const float k = s.dt * s.inv_dx;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          G[r * 3 + q] = (r == q ? 1.0f : 0.0f) +
+                         k * (Bh[r * 3 + 0] * Di[0 * 3 + q] + Bh[r * 3 + 1] * Di[1 * 3 + q] + Bh[r * 3 + 2] * Di[2 * 3 + q]);
+      const float Fo[9] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2};
+      float F[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          F[r * 3 + q] = G[r * 3 + 0] * Fo[0 * 3 + q] + G[r * 3 + 1] * Fo[1 * 3 + q] + G[r * 3 + 2] * Fo[2 * 3 + q];
+      // constitutive update; float64 redo for degenerate F (precision extension)
+      float tau[9];
+      {
+        float U[9], V[9], sg[3];
+        svd3<float>(F, U, sg, V);
+        float a0 = fabsf(sg[0]), a1 = fabsf(sg[1]), a2 = fabsf(sg[2]);
+        float smax = fmaxf(a0, fmaxf(a1, a2));
+        float smin = min3(a0, a1, a2);
+        float J = sg[0] * sg[1] * sg[2];
+        float gap = min3(fabsf(a0 - a1), fabsf(a0 - a2), fabsf(a1 - a2));
+        bool use64 = (fabsf(J) < s.j_tol) || (smin < s.cond_tol * smax) || (gap < s.gap_tol * smax);
+        if (use64) {
+          double Fd[9], taud[9], sgd[3];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) Fd[q] = (double)F[q];
+          constitutive<double>(mt.model, Fd, (double)mu, (double)lam, (double)mt.alpha, taud, sgd);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            F[q] = (float)Fd[q];
+            tau[q] = (float)taud[q];
+          }
+          atomicAdd(v.fp64_count, 1ull);
+        } else {
+          if (mt.model == 1) {
+            if (dp_project<float>(sg, mu, lam, mt.alpha)) usvt<float>(U, sg, V, F);
+            hencky_tau<float>(U, sg, mu, lam, tau);
+          } else {
+            fc_tau<float>(F, U, sg, V, mu, lam, tau);
+          }
+        }
+      }
+      // M' = m B' - dt V0 tau, B' = dx Bh
+      const float mdx = mt.mass * s.dx, dtv = s.dt * s.V0;
+      float Mn[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Mn[q] = mdx * Bh[q] - dtv * tau[q];
+      float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
+      // next key; particles leaving the interior are clamped and flagged
+      float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
+      bool fin = isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(vx) && isfinite(vy) && isfinite(vz);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]);
+      if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
+      if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {
+        flag_error(v.err, CK_ERR_DOMAIN);
+        const float lo = 0.5f, hi = (float)s.res - 0.5f - 1e-3f;
+        ux = fminf(fmaxf(isfinite(ux) ? ux : lo, lo), hi);
+        uy = fminf(fmaxf(isfinite(uy) ? uy : lo, lo), hi);
+        uz = fminf(fmaxf(isfinite(uz) ? uz : lo, lo), hi);
+        Xn.x = ux * s.dx;
+        Xn.y = uy * s.dx;
+        Xn.z = uz * s.dx;
+        ux = Xn.x * s.inv_dx;
+        uy = Xn.y * s.inv_dx;
+        uz = Xn.z * s.inv_dx;
+      }
+      const uint32_t nk = particle_key<KIND>(s, ux, uy, uz);
+      v.nxt.X[t] = Xn;
+      v.nxt.VM0[t] = make_float4(vx, vy, vz, Mn[0]);
+      v.nxt.VM1[t] = make_float4(Mn[1], Mn[2], Mn[3], Mn[4]);
+      v.nxt.VM2[t] = make_float4(Mn[5], Mn[6], Mn[7], Mn[8]);
+      v.nxt.F0[t] = make_float4(F[0], F[1], F[2], F[3]);
+      v.nxt.F1[t] = make_float4(F[4], F[5], F[6], F[7]);
+      v.nxt.F2[t] = F[8];
+      v.nxt.ID[t] = id;
+      if (v.nxt.E) v.nxt.E[t] = Ep;
+      v.key_nxt[t] = nk;
+      warp_aggregated_inc(v.cnt_nxt, nk);
+    }
+    __syncthreads();
+  }
+}
+
+// Zero the accumulators of the blocks listed by the last probe.
+template <int KIND>
+__global__ void k_clear_gacc(StepView v) {
+  constexpr int NG = Geo<KIND>::NG;
+  const uint32_t ng = *v.n_g;
+  for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+    const uint32_t g = v.g_list[gi];
+    for (int t = threadIdx.x; t < NG * kBlockNodes; t += blockDim.x)
+      v.Gacc[((long long)g * NG + (t / kBlockNodes)) * kBlockNodes + (t % kBlockNodes)] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ------------------------------------------------------- readback / upload
+
+__device__ __forceinline__ void load_F(const Pool& P, uint32_t t, float* F) {
+  float4 a = P.F0[t], b = P.F1[t];
+  F[0] = a.x; F[1] = a.y; F[2] = a.z; F[3] = a.w;
+  F[4] = b.x; F[5] = b.y; F[6] = b.z; F[7] = b.w;
+  F[8] = P.F2[t];
+}
+
+__device__ __forceinline__ void load_M(const Pool& P, uint32_t t, float* M) {
+  float4 a = P.VM0[t], b = P.VM1[t], c = P.VM2[t];
+  M[0] = a.w; M[1] = b.x; M[2] = b.y; M[3] = b.z;
+  M[4] = b.w; M[5] = c.x; M[6] = c.y; M[7] = c.z; M[8] = c.w;
+}
+
+__device__ __forceinline__ void store_M(Pool& P, uint32_t t, const float* M) {
+  float4 a = P.VM0[t];
+  a.w = M[0];
+  P.VM0[t] = a;
+  P.VM1[t] = make_float4(M[1], M[2], M[3], M[4]);
+  P.VM2[t] = make_float4(M[5], M[6], M[7], M[8]);
+}
+
+__device__ __forceinline__ void lame_of(const MatDev& mt, const Pool& P, uint32_t t, float& mu, float& lam) {
+  mu = mt.mu;
+  lam = mt.lam;
+  if (P.E) {
+    float E = P.E[t];
+    mu = E / (2.0f * (1.0f + mt.nu));
+    lam = E * mt.nu / ((1.0f + mt.nu) * (1.0f - 2.0f * mt.nu));
+  }
+}
+
+// B = (M + dt V0 tau(F)) / m
+__device__ __forceinline__ void recover_B(const Pool& P, const SceneDev& s, const MatDev& mt, uint32_t t, float* B) {
+  float F[9], M[9], tau[9];
+  load_F(P, t, F);
+  load_M(P, t, M);
+  float mu, lam;
+  lame_of(mt, P, t, mu, lam);
+  stress_only<float>(mt.model, F, mu, lam, tau);
+  float dtv = s.dt * s.V0, im = 1.0f / mt.mass;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) B[q] = (M[q] + dtv * tau[q]) * im;
+}
+
+template <int KIND>
+__global__ void k_read_particles(Pool P, const SceneDev* scenes, const MatDev* mats, int scene, uint32_t start,
+                                 uint32_t n, int field, float* out) {
+  const SceneDev s = scenes[scene];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t t = start + i;
+    uint32_t id = P.ID[t];
+    float4 X = P.X[t];
+    const MatDev mt = mats[__float_as_uint(X.w)];
+    if (field == 0) {
+      out[3 * id] = X.x; out[3 * id + 1] = X.y; out[3 * id + 2] = X.z;
+    } else if (field == 1) {
+      float4 a = P.VM0[t];
+      out[3 * id] = a.x; out[3 * id + 1] = a.y; out[3 * id + 2] = a.z;
+    } else if (field == 4) {
+      float F[9];
+      load_F(P, t, F);
+      for (int q = 0; q < 9; ++q) out[9 * id + q] = F[q];
+    } else if (field == 5) {
+      out[id] = P.E ? P.E[t] : 0.f;
+    } else {
+      float B[9];
+      recover_B(P, s, mt, t, B);
+      if (field == 2) {
+        for (int q = 0; q < 9; ++q) out[9 * id + q] = B[q];
+      } else {  // C = B D^-1 = B Di / dx^2
+        Sten<KIND> st;
+        float ux = X.x * s.inv_dx, uy = X.y * s.inv_dx, uz = X.z * s.inv_dx;
+        Cell<KIND> cx, cy, cz;
+        cx.set(ux); cy.set(uy); cz.set(uz);
+        st.set(ux, uy, uz, cx.block() * 4, cy.block() * 4, cz.block() * 4);
+        float Di[9];
+        dinv_of<KIND>(st, Di);
+        float k = s.inv_dx * s.inv_dx;
+        for (int r = 0; r < 3; ++r)
+          for (int q = 0; q < 3; ++q)
+            out[9 * id + r * 3 + q] = k * (B[r * 3] * Di[q] + B[r * 3 + 1] * Di[3 + q] + B[r * 3 + 2] * Di[6 + q]);
+      }
+    }
+  }
+}
+
+// Overwrite one field from original-order input; keeps M = m B - dt V0 tau(F).
+__global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* mats, int scene, uint32_t start,
+                                  uint32_t n, int field, const float* in) {
+  const SceneDev s = scenes[scene];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t t = start + i;
+    uint32_t id = P.ID[t];
+    float4 X = P.X[t];
+    const MatDev mt = mats[__float_as_uint(X.w)];
+    float dtv = s.dt * s.V0;
+    if (field == 0) {
+      P.X[t] = make_float4(in[3 * id], in[3 * id + 1], in[3 * id + 2], X.w);
+    } else if (field == 1) {
+      float4 a = P.VM0[t];
+      P.VM0[t] = make_float4(in[3 * id], in[3 * id + 1], in[3 * id + 2], a.w);
+    } else if (field == 2) {
+      float F[9], tau[9], M[9], mu, lam;
+      load_F(P, t, F);
+      lame_of(mt, P, t, mu, lam);
+      stress_only<float>(mt.model, F, mu, lam, tau);
+      for (int q = 0; q < 9; ++q) M[q] = mt.mass * in[9 * id + q] - dtv * tau[q];
+      store_M(P, t, M);
+    } else if (field == 4 || field == 5) {
+      float B[9];
+      recover_B(P, s, mt, t, B);
+      if (field == 4) {
+        P.F0[t] = make_float4(in[9 * id], in[9 * id + 1], in[9 * id + 2], in[9 * id + 3]);
+        P.F1[t] = make_float4(in[9 * id + 4], in[9 * id + 5], in[9 * id + 6], in[9 * id + 7]);
+        P.F2[t] = in[9 * id + 8];
+      } else if (P.E) {
+        P.E[t] = in[id];
+      }
+      float F[9], tau[9], M[9], mu, lam;
+      load_F(P, t, F);
+      lame_of(mt, P, t, mu, lam);
+      stress_only<float>(mt.model, F, mu, lam, tau);
+      for (int q = 0; q < 9; ++q) M[q] = mt.mass * B[q] - dtv * tau[q];
+      store_M(P, t, M);
+    }
+  }
+}
+
+// Dense grid fields of one scene: out[slot][iz][iy][ix] (x fastest) over
+// 0..res per axis; which: 0 mass, 1 momentum (3), 2 velocity (3).
+template <int KIND>
+__global__ void k_read_grid(const float4* Gacc, const float4* Gvel, const SceneDev* scenes, int scene, int which,
+                            float* out) {
+  const SceneDev s = scenes[scene];
+  const int n = s.res + 1;
+  const long long total = (long long)Geo<KIND>::NG * n * n * n;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    int slot = (int)(q / ((long long)n * n * n));
+    long long r = q % ((long long)n * n * n);
+    int ix = (int)(r % n), iy = (int)((r / n) % n), iz = (int)(r / ((long long)n * n));
+    long long gi = arena_index<KIND>(s, slot, ix, iy, iz);
+    float4 a = Gacc[gi];
+    if (which == 0) {
+      out[q] = a.x;
+    } else if (which == 1) {
+      out[3 * q] = a.y; out[3 * q + 1] = a.z; out[3 * q + 2] = a.w;
+    } else {
+      float4 g = Gvel[gi];
+      bool has = a.x > 0.f;
+      out[3 * q] = has ? g.x : 0.f;
+      out[3 * q + 1] = has ? g.y : 0.f;
+      out[3 * q + 2] = has ? g.z : 0.f;
+    }
+  }
+}
+
+// Append a new scene's particles: X (x, mat_base + mat), v, M = 0 (B = 0 and
+// tau(I) = 0), F = I, ID = index; plus keys and the histogram.
+template <int KIND>
+__global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene, uint32_t mat_base,
+                        uint32_t nmat, uint32_t start, uint32_t n, const float* x, const float* vel, const uint8_t* mat,
+                        const float* E, uint32_t* err) {
+  const SceneDev s = scenes[scene];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t t = start + i;
+    float px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    float ux = px * s.inv_dx, uy = py * s.inv_dx, uz = pz * s.inv_dx;
+    if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {
+      flag_error(err, CK_ERR_DOMAIN);
+      const float lo = 0.5f, hi = (float)s.res - 0.5f - 1e-3f;
+      ux = fminf(fmaxf(isfinite(ux) ? ux : lo, lo), hi);
+      uy = fminf(fmaxf(isfinite(uy) ? uy : lo, lo), hi);
+      uz = fminf(fmaxf(isfinite(uz) ? uz : lo, lo), hi);
+      px = ux * s.dx; py = uy * s.dx; pz = uz * s.dx;
+      ux = px * s.inv_dx; uy = py * s.inv_dx; uz = pz * s.inv_dx;
+    }
+    uint32_t mloc = mat ? (uint32_t)mat[i] : 0u;
+    if (mloc >= nmat) {  // unknown material index: use material 0 and report
+      flag_error(err, CK_ERR_INTERNAL);
+      mloc = 0;
+    }
+    uint32_t m = mat_base + mloc;
+    P.X[t] = make_float4(px, py, pz, __uint_as_float(m));
+    float vx = vel ? vel[3 * i] : 0.f, vy = vel ? vel[3 * i + 1] : 0.f, vz = vel ? vel[3 * i + 2] : 0.f;
+    P.VM0[t] = make_float4(vx, vy, vz, 0.f);
+    P.VM1[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    P.VM2[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    P.F0[t] = make_float4(1.f, 0.f, 0.f, 0.f);
+    P.F1[t] = make_float4(1.f, 0.f, 0.f, 0.f);
+    P.F2[t] = 1.f;
+    P.ID[t] = i;
+    if (P.E) P.E[t] = E ? E[i] : 0.f;
+    uint32_t k = particle_key<KIND>(s, ux, uy, uz);
+    key[t] = k;
+    warp_aggregated_inc(cnt, k);
+  }
+}
+
+// Recompute keys and the histogram of the whole current pool (after an
+// upload of positions or a release); particles of released scenes get the
+// dead key and leave the pool at the next step.
+template <int KIND>
+__global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, const MatDev* mats, uint32_t n,
+                        uint32_t* err) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    float4 X = P.X[t];
+    const MatDev mt = mats[__float_as_uint(X.w)];
+    const SceneDev s = scenes[mt.scene];
+    if (!s.alive) {
+      key[t] = CK_DEAD_KEY;
+      continue;
+    }
+    float ux = X.x * s.inv_dx, uy = X.y * s.inv_dx, uz = X.z * s.inv_dx;
+    if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {
+      flag_error(err, CK_ERR_DOMAIN);
+      const float lo = 0.5f, hi = (float)s.res - 0.5f - 1e-3f;
+      ux = fminf(fmaxf(isfinite(ux) ? ux : lo, lo), hi);
+      uy = fminf(fmaxf(isfinite(uy) ? uy : lo, lo), hi);
+      uz = fminf(fmaxf(isfinite(uz) ? uz : lo, lo), hi);
+      X.x = ux * s.dx; X.y = uy * s.dx; X.z = uz * s.dx;
+      P.X[t] = X;
+      ux = X.x * s.inv_dx; uy = X.y * s.inv_dx; uz = X.z * s.inv_dx;
+    }
+    uint32_t k = particle_key<KIND>(s, ux, uy, uz);
+    key[t] = k;
+    warp_aggregated_inc(cnt, k);
+  }
+}
+
+// ------------------------------------------------------------ host launchers
+
+template <int KIND>
+static void launch_all(const LaunchCfg& lc, StepView v, int which) {
+  switch (which) {
+    case LK_P2G: k_p2g<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+    case LK_UPDATE: k_grid_update<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+    case LK_G2P: k_g2p<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+    case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+  }
+}
+
+void launch_transfer(int kind, const LaunchCfg& lc, const StepView& v, int which) {
+  if (kind == 0)
+    launch_all<0>(lc, v, which);
+  else
+    launch_all<1>(lc, v, which);
+}
+
+void launch_read_particles(int kind, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
+                           uint32_t start, uint32_t n, int field, float* out) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  if (kind == 0)
+    k_read_particles<0><<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, out);
+  else
+    k_read_particles<1><<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, out);
+}
+
+void launch_write_particles(cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
+                            uint32_t start, uint32_t n, int field, const float* in) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  k_write_particles<<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, in);
+}
+
+void launch_read_grid(int kind, cudaStream_t st, const float4* Gacc, const float4* Gvel, const SceneDev* scenes,
+                      int scene, int which, float* out, long long total) {
+  int blocks = (int)((total + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 8192) blocks = 8192;
+  if (kind == 0)
+    k_read_grid<0><<<blocks, 256, 0, st>>>(Gacc, Gvel, scenes, scene, which, out);
+  else
+    k_read_grid<1><<<blocks, 256, 0, st>>>(Gacc, Gvel, scenes, scene, which, out);
+}
+
+void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene,
+                  uint32_t mat_base, uint32_t nmat, uint32_t start, uint32_t n, const float* x, const float* v,
+                  const uint8_t* mat, const float* E, uint32_t* err) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 8192) blocks = 8192;
+  if (kind == 0)
+    k_admit<0><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, scene, mat_base, nmat, start, n, x, v, mat, E, err);
+  else
+    k_admit<1><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, scene, mat_base, nmat, start, n, x, v, mat, E, err);
+}
+
+void launch_rekey(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes,
+                  const MatDev* mats, uint32_t n, uint32_t* err) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 8192) blocks = 8192;
+  if (kind == 0)
+    k_rekey<0><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, mats, n, err);
+  else
+    k_rekey<1><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, mats, n, err);
+}
+
+}  // namespace ck

@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the CK-MPM step on GB300 (prints one JSON line).
+
+Workload: the 16,273,664-particle large-impact scene on a 512^3 virtual grid
+(Drucker-Prager sand castle hit by four stiff fixed-corotated balls, dt 2e-5).
+One step = binning + P2G + grid update + fused G2P/constitutive for every
+particle.  Metric: particle-steps/s (whole job); the quadratic B-spline path
+runs the same scene for comparison, and a short served mix reports p50/p99
+step latency.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload.  With torchrun (N > 1) every rank runs its own
+replica of the scene (weak scaling, no collective on the data path); rank 0
+prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 16M particles vs quadratic B-spline; served step p50/p99"
+UNIT = "particle-steps/s"
+WORKLOAD = "large_impact: 512^3 virtual grid (dx 1/512), DP sand castle + 4 FC balls (E 1e7) at 20 m/s, 16,273,664 particles, 8 ppc, dt 2e-5"
+
+# Algorithmic bytes per particle of each kernel (float32 state):
+#   P2G: read x 12 + v 12 + M 36 B, write 2 grids x 16 B per node at 1/8 node per particle = 4 B -> 64 B
+#   G2P: read x 12 + F 36, gather 2 grids x 12 B / 8 = 3, write x 12 + v 12 + M 36 + F 36 -> 147 B
+#   grid update: per node read 16 + write 12 B, 2 grids / 8 -> 7 B
+ALGO_BYTES = {"p2g": 64.0, "g2p": 147.0, "grid_update": 7.0}
+KERNEL_SLOT = {"bin": 0, "scatter": 1, "p2g": 2, "grid_update": 3, "g2p": 4, "grid_list": 5}
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2412_10399_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{kernel}_large_impact.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != _source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        t0 = time.time()  # wait for the first sample so the timed region is covered
+        while time.time() - t0 < 10 and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+            time.sleep(0.05)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------- CPU leg
+
+def _cpu_sample():
+    """A bounded sample of the workload for the FP64 oracle: the castle base in
+    a 64 x 32 x 64-cell window (cells [160,224) x [4,36) x [160,224) of the
+    512^3 scene), shifted into its own 80^3 domain with the same dx, dt and
+    material: 1,048,576 particles."""
+    from paper_2412_10399_gb300 import scenes as S
+    res = 512
+    dx = 1.0 / res
+    cells = S.filled_cells([S._box([160, 4, 160], [224, 36, 224])], res)
+    x = S.sample_cells(cells, res, dx, seed=0)
+    x = x - np.array([152, 0, 152]) * dx
+    sc = S.Scene("large_impact_window", 80, dx, 2e-5, x, np.zeros_like(x), np.zeros(len(x), np.uint8),
+                 [S.SAND], steps=2)
+    return sc
+
+
+def cpu_baseline(steps: int = 2):
+    import torch
+    from oracle import ckmpm_oracle as O
+    sc = _cpu_sample()
+    prm = O.params_from_scene(sc)
+    st = O.state_from_scene(sc)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = O.step(st, prm)
+    dt = time.perf_counter() - t0
+    return {"value": sc.n * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{sc.n} particles (castle-base window of the 16.27M scene, same dx/dt/material), "
+                      f"{steps} FP64 steps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    warm = max(0, min(args.warmup, 1))
+    if warm:
+        cpu_baseline(steps=1)
+    cb = cpu_baseline(steps=min(steps, 3))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": min(steps, 3), "warmup": warm, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU leg
+
+def _make_ctx(ck, scene, kernel, stream, timing=False):
+    sc, keep = ck.scene_struct(scene)
+    ctx = ck.ckmpm_create(sc, kernel, stream)
+    if timing:
+        ck.ckmpm_set_timing(ctx, True)
+    return ctx, keep
+
+
+def _time_steps(ck, ctx, steps, stream_ptr):
+    import torch
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    ck.ckmpm_step(ctx, steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0):
+    """Continuous batching of a Poisson stream of scenes in one context: each
+    global step advances every resident scene; arrivals are admitted between
+    steps as capacity allows; completed scenes are released.  Returns p50/p99
+    of the per-scene step latency (the device time of the global step each
+    scene step belonged to) and the aggregate particle-steps/s."""
+    import torch
+    from paper_2412_10399_gb300 import scenes as S
+    reqs = S.served_mix(n_scenes=n_scenes, seed=seed, n_max=2e6 * scale, steps=steps)
+    cap_n = int(sum(r.scene.n for r in reqs) * 0.6) + 1
+    nb = (128 // 4 + 1) ** 3
+    cfg = ck.ckmpm_config()
+    cfg.kernel = ck.KERNEL_CK
+    cfg.max_particles = cap_n
+    cfg.max_keys = (128 // 4) ** 3 * 8
+    cfg.max_grid_blocks = nb * 8
+    cfg.max_scenes = 8
+    cfg.max_materials = 64
+    cfg.stream = stream_ptr
+    ctx = ck.ckmpm_create_server(cfg)
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    pending = list(reqs)
+    resident = {}  # scene id -> [remaining steps, n, keep]
+    lat = []
+    total_ps = 0
+    t_start = time.perf_counter()
+    wall0 = time.perf_counter()
+    busy_ms = 0.0
+    while pending or resident:
+        now = time.perf_counter() - t_start
+        while pending and pending[0].arrival_s * 0.05 <= now:
+            r = pending[0]
+            sc, keep = ck.scene_struct(r.scene)
+            try:
+                sid = ck.ckmpm_admit(ctx, sc)
+            except ck.CKMPMError as e:
+                if e.status == ck.ENOMEM:
+                    break
+                raise
+            resident[sid] = [r.scene.steps, r.scene.n, keep]
+            pending.pop(0)
+        if not resident:
+            time.sleep(0.001)
+            continue
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ck.ckmpm_step(ctx, 1)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        busy_ms += ms
+        for sid in list(resident):
+            lat.append(ms)
+            total_ps += resident[sid][1]
+            resident[sid][0] -= 1
+            if resident[sid][0] == 0:
+                ck.ckmpm_release(ctx, sid)
+                del resident[sid]
+    ck.ckmpm_sync(ctx)
+    wall = time.perf_counter() - wall0
+    ck.ckmpm_destroy(ctx)
+    lat.sort()
+    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "scene_steps": len(lat), "scenes": n_scenes, "steps_per_scene": steps,
+            "aggregate_particle_steps_per_s": total_ps / (busy_ms / 1e3),
+            "wall_particle_steps_per_s": total_ps / wall,
+            "mix": f"{n_scenes} scenes, N log-uniform in [1e4, {2e6 * scale:.0f}], box/sphere, elastic or sand, "
+                   f"{steps} steps each, arrivals Poisson (20 ms mean, time-compressed x20)"}
+
+
+def run_gpu(args):
+    import torch
+    rank, local_rank, world = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2412_10399_gb300 import ckmpm as ck
+    from paper_2412_10399_gb300 import scenes as S
+
+    stream_ptr = torch.cuda.Stream().cuda_stream
+    scene = S.large_impact(seed=rank)
+    if args.max_particles and args.max_particles < scene.n:
+        k = args.max_particles
+        scene.x, scene.v, scene.mat = scene.x[:k], scene.v[:k], scene.mat[:k]
+    n = scene.n
+
+    # ---------------- device-resident timing of the CK path
+    ctx, keep = _make_ctx(ck, scene, ck.KERNEL_CK, stream_ptr)
+    ck.ckmpm_step(ctx, args.warmup)
+    ck.ckmpm_sync(ctx)
+    ck.ckmpm_set_timing(ctx, True)
+    ck.ckmpm_reset_timing(ctx)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms = _time_steps(ck, ctx, args.steps, stream_ptr)
+    clocks = sampler.stop()
+    ck.ckmpm_sync(ctx)
+    st = ck.ckmpm_get_stats(ctx)
+    ck.ckmpm_set_timing(ctx, False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    per_kernel = {k: st.ms_kernel[i] for k, i in KERNEL_SLOT.items()}
+    launches = int(st.launches_per_step) * args.steps
+    fp64_frac = st.fp64_particles / max(1, n)
+    n_pb, n_gb = int(st.n_particle_blocks), int(st.n_grid_blocks)
+    ck.ckmpm_destroy(ctx)
+
+    value = world * n * args.steps / (ms / 1e3)
+    dominant = max(("p2g", "g2p"), key=lambda k: per_kernel[k])
+    peak, peak_src = _peaks()
+    achieved = ALGO_BYTES[dominant] * n / (per_kernel[dominant] / 1e3) / 1e9
+    traffic = _traffic(dominant)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "algorithmic_bytes_per_particle": ALGO_BYTES[dominant], "traffic": traffic,
+                "per_kernel_ms": per_kernel,
+                "step_algorithmic_bytes_per_particle": sum(ALGO_BYTES.values()),
+                "step_frac": sum(ALGO_BYTES.values()) * n / (ms / args.steps / 1e3) / 1e9 / peak}
+
+    # ---------------- quadratic B-spline twin on the same inputs
+    qsteps = max(3, args.steps // 2)
+    ctxq, keepq = _make_ctx(ck, scene, ck.KERNEL_QUADRATIC, stream_ptr)
+    ck.ckmpm_step(ctxq, max(1, args.warmup))
+    ck.ckmpm_sync(ctxq)
+    msq = _time_steps(ck, ctxq, qsteps, stream_ptr)
+    ck.ckmpm_sync(ctxq)
+    ck.ckmpm_destroy(ctxq)
+    quad = {"value": n * qsteps / (msq / 1e3), "ms_per_step": msq / qsteps, "steps": qsteps,
+            "ck_speedup": (msq / qsteps) / (ms / args.steps)}
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    e2e_steps = max(2, min(args.steps, 10))
+    xh = torch.from_numpy(scene.x32()).pin_memory()
+    vh = torch.from_numpy(scene.v32()).pin_memory()
+    mh = torch.from_numpy(scene.mat.copy()).pin_memory()
+    out = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    cfg = ck.ckmpm_config()
+    cfg.kernel = ck.KERNEL_CK
+    cfg.max_particles = n
+    cfg.max_keys = 128 ** 3
+    cfg.max_grid_blocks = 129 ** 3
+    cfg.max_scenes = 1
+    cfg.max_materials = len(scene.materials)
+    cfg.stream = stream_ptr
+    srv = ck.ckmpm_create_server(cfg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sc, keep2 = ck.make_scene(scene.res, scene.dx, scene.dt, scene.materials, xh.numpy(), vh.numpy(),
+                              mh.numpy(), gravity=scene.gravity, bc_cells=scene.bc_cells, ppc=scene.ppc)
+    sid = ck.ckmpm_admit(srv, sc)
+    for _ in range(e2e_steps):
+        ck.ckmpm_step(srv, 1)
+        ck.ckmpm_readback(srv, sid, ck.FIELD_X, out.data_ptr(), out.numel() * 4, False)
+    ck.ckmpm_release(srv, sid)
+    ck.ckmpm_sync(srv)
+    t_e2e = time.perf_counter() - t0
+    ck.ckmpm_destroy(srv)
+    e2e = {"value": world * n * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int((xh.numel() * 4 + vh.numel() * 4 + mh.numel()) / e2e_steps),
+           "d2h_bytes_per_step": int(out.numel() * 4), "steps": e2e_steps,
+           "how": "admit from pinned host x/v/mat, then per step: ckmpm_step + readback of positions to pinned host"}
+
+    served = served_mix(ck, stream_ptr) if not args.no_served else None
+    cb = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "particles_per_gpu": n, "particle_blocks": n_pb,
+                           "grid_blocks": n_gb, "l2": "inputs larger than L2 (about 3.7 GB of particle state)",
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "fp64_svd_fraction": fp64_frac},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "quadratic": quad, "served": served}
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--max-particles", type=int, default=0,
+                    help="keep only the first N particles of the scene (a slab of the castle base; "
+                         "for profiling a smaller case)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -27,6 +27,7 @@ struct Num<float> {
   __device__ static __forceinline__ float hypot_(float a, float b) { return hypotf(a, b); }
   static constexpr int sweeps = 5;
   static constexpr float huge_theta = 1e15f;
+  static constexpr float eps = 5.9604645e-8f;  // 2^-24
 };
 template <>
 struct Num<double> {
@@ -38,15 +39,24 @@ struct Num<double> {
   __device__ static __forceinline__ double hypot_(double a, double b) { return hypot(a, b); }
   static constexpr int sweeps = 8;
   static constexpr double huge_theta = 1e150;
+  static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
 };
 
 // Row-major 3x3 helpers.
 #define CK_M(a, i, j) (a)[(i)*3 + (j)]
 
+// Jacobi rotation zeroing S[p][q].  An off-diagonal below half an ulp of the
+// diagonal is dropped without rotating: rotating it away (a 45 degree turn
+// when S[p][p] ~ S[q][q], e.g. F ~ I) changes nothing exact but rounds the
+// rotation's c and s and puts an ulp of noise into the singular values.
 template <typename T>
 __device__ __forceinline__ void jacobi_rotate(T* S, T* V, int p, int q, int r) {
   T apq = CK_M(S, p, q);
-  if (apq == T(0)) return;
+  if (Num<T>::abs_(apq) <= Num<T>::eps * (Num<T>::abs_(CK_M(S, p, p)) + Num<T>::abs_(CK_M(S, q, q)))) {
+    CK_M(S, p, q) = T(0);
+    CK_M(S, q, p) = T(0);
+    return;
+  }
   T theta = (CK_M(S, q, q) - CK_M(S, p, p)) / (T(2) * apq);
   T at = Num<T>::abs_(theta);
   T t = at > Num<T>::huge_theta ? T(0.5) / theta

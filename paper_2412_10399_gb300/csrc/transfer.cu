@@ -224,7 +224,15 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
       sm[3][j] = 0.f;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    // Lanes of a warp take particles C = ceil(cnt/32) apart in the block's
+    // order.  Particles of one cell sit next to each other (sampling order,
+    // kept by the binning), so neighbouring lanes come from different cells
+    // and their shared-memory atomics hit different nodes instead of
+    // serialising on the same address.
+    const uint32_t C = (cnt + 31u) >> 5;
+    for (uint32_t q = threadIdx.x; q < (C << 5); q += blockDim.x) {
+      const uint32_t i = (q & 31u) * C + (q >> 5);
+      if (i >= cnt) continue;
       const uint32_t p = v.perm[start + i];
       const float4 X = v.cur.X[p];
       const float4 a = v.cur.VM0[p];

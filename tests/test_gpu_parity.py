@@ -114,7 +114,16 @@ def test_granular_column_steps(kernel):
     prm = O.params_from_scene(sc)
     st = O.run(O.state_from_scene(sc), prm, 10)
     assert np.abs(x - st.x.numpy()).max() <= 1e-4 * sc.dx
-    assert rel(v, st.v.numpy()) <= 1e-4
+    # float32 singular values of F ~ I carry a few ulp (4 ulp of 1.0 = 4.8e-7) of
+    # noise, so the Hencky stress carries (2 mu + 3 lam) * 4.8e-7 ~ 0.4 Pa of
+    # noise; at a free surface that accelerates particles by ~tau / (rho dx) and
+    # over n steps moves v by n dt tau / (rho dx) ~ 3e-5 m/s here (the oracle,
+    # in float64, has exact zeros for the lateral velocity of the falling column).
+    mat = sc.materials[0]
+    mu = mat.E / (2 * (1 + mat.nu))
+    lam = mat.E * mat.nu / ((1 + mat.nu) * (1 - 2 * mat.nu))
+    bound = 10 * sc.dt * (2 * mu + 3 * lam) * 4.8e-7 / (mat.rho * sc.dx)
+    assert np.abs(v - st.v.numpy()).max() <= bound
 
 
 @pytest.mark.parametrize("kernel", KERNELS)

@@ -234,7 +234,8 @@ def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0):
     cfg.kernel = ck.KERNEL_CK
     cfg.max_particles = cap_n
     cfg.max_keys = (128 // 4) ** 3 * 8
-    cfg.max_grid_blocks = nb * 8
+    cfg.max_virtual_blocks = nb * 8
+    cfg.max_grid_blocks = cap_n // 64 + 8 * 4096
     cfg.max_scenes = 8
     cfg.max_materials = 64
     cfg.stream = stream_ptr
@@ -372,7 +373,8 @@ def run_gpu(args):
     cfg.kernel = ck.KERNEL_CK
     cfg.max_particles = n
     cfg.max_keys = 128 ** 3
-    cfg.max_grid_blocks = 129 ** 3
+    cfg.max_virtual_blocks = 129 ** 3
+    cfg.max_grid_blocks = n // 64 + 4096
     cfg.max_scenes = 1
     cfg.max_materials = len(scene.materials)
     cfg.stream = stream_ptr

@@ -108,7 +108,8 @@ typedef struct {
   int kernel;                  /* ckmpm_kernel; fixed for the context */
   int64_t max_particles;       /* particle pool capacity */
   int64_t max_keys;            /* particle-block key space (sum over scenes of ceil(res/4)^3) */
-  int64_t max_grid_blocks;     /* grid arena capacity in 4x4x4-node blocks (sum of (ceil(res/4)+1)^3) */
+  int64_t max_grid_blocks;     /* grid pool: 4x4x4-node blocks active at once, all scenes together */
+  int64_t max_virtual_blocks;  /* block-table entries (sum over scenes of (ceil(res/4)+1)^3) */
   int max_scenes;              /* resident scene slots (<= 1024) */
   int max_materials;           /* material table entries (<= 65535) */
   int per_particle_E;          /* 1: keep a per-particle Young's modulus (differentiation) */

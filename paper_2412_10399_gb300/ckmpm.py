@@ -50,7 +50,8 @@ class ckmpm_allocator(ctypes.Structure):
 
 class ckmpm_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("max_particles", ctypes.c_int64), ("max_keys", ctypes.c_int64),
-                ("max_grid_blocks", ctypes.c_int64), ("max_scenes", ctypes.c_int),
+                ("max_grid_blocks", ctypes.c_int64), ("max_virtual_blocks", ctypes.c_int64),
+                ("max_scenes", ctypes.c_int),
                 ("max_materials", ctypes.c_int), ("per_particle_E", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("allocator", ctypes.POINTER(ckmpm_allocator))]
 

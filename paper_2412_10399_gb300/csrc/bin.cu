@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
       for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
           for (int dx = 0; dx < 2; ++dx)
-            v.gflag[s.grid_base + ((long long)(bz + dz) * s.nb + (by + dy)) * s.nb + (bx + dx)] = (uint32_t)sl + 1u;
+            v.gflag[s.table_base + ((long long)(bz + dz) * s.nb + (by + dy)) * s.nb + (bx + dx)] = (uint32_t)sl + 1u;
       pn += 1;
     }
     pc += c[q];
@@ -195,13 +195,22 @@ __global__ void k_scatter(StepView v) {
   }
 }
 
-__global__ void k_glist(StepView v, uint32_t n_gblocks) {
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_gblocks; g += gridDim.x * blockDim.x) {
+// Flagged virtual blocks get pool slots in list order; the block table maps
+// each of them to its slot.  Entries of untouched blocks are stale and never
+// read (P2G/G2P only look up the blocks their own particle block flagged).
+__global__ void k_glist(StepView v, uint32_t n_vblocks) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_vblocks; g += gridDim.x * blockDim.x) {
     uint32_t f = v.gflag[g];
     if (f) {
       uint32_t idx = warp_aggregated_inc(v.n_g, 0u);
-      v.g_list[idx] = g;
-      v.g_scene[idx] = f - 1u;
+      if (idx < v.pool_cap) {
+        v.g_list[idx] = g;
+        v.g_scene[idx] = f - 1u;
+        v.table[g] = idx;
+      } else {
+        v.table[g] = CK_NO_SLOT;
+        flag_error(v.err, CK_ERR_POOL);
+      }
       v.gflag[g] = 0u;
     }
   }

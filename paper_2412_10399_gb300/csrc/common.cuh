@@ -10,10 +10,13 @@
 // stress force (Sec. 4.3.2 with reading R4).  Storing M instead of B lets P2G
 // run without an SVD; B is recovered exactly as (M + dt V0 tau(F)) / m.
 //
-// Grid arena: blocks of 4x4x4 nodes; per block and grid slot 64 float4.
+// Sparse grid: each scene's domain is a virtual array of 4x4x4-node blocks;
+// a block table maps the blocks touched this step to slots of a compact pool
+// (slot = position in the active-block list, reassigned every step).  Per
+// pool slot and grid 64 float4:
 //   Gacc  (m, p_x, p_y, p_z) accumulated by P2G, zeroed by the grid update
 //   Gvel  (v~_x, v~_y, v~_z, m) written by the grid update, gathered by G2P
-// CK uses two grid slots per block (0: G-, 1: G+), quadratic one.
+// CK uses two grids per block (0: G-, 1: G+), quadratic one.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -22,6 +25,8 @@
 #define CK_ERR_NONFINITE 2u
 #define CK_ERR_INTERNAL 4u
 #define CK_ERR_TIMEOUT 8u
+#define CK_ERR_POOL 16u
+#define CK_NO_SLOT 0xFFFFFFFFu
 
 #define CK_DEAD_KEY 0xFFFFFFFFu
 
@@ -38,7 +43,7 @@ struct SceneDev {
   int npb;            // particle blocks per axis = ceil(res/4)
   int nb;             // grid blocks per axis = npb + 1
   uint32_t key_base;  // first particle-block key of this scene
-  long long grid_base;  // first grid block of this scene in the arena
+  long long table_base;  // first entry of this scene's block table
   float j_tol, cond_tol, gap_tol;  // float64 SVD criteria
   int alive;
 };
@@ -78,10 +83,12 @@ struct StepView {
   uint32_t* pb_key;     // non-empty particle blocks: key
   uint32_t* pb_scene;   // and owning scene
   uint32_t* n_pb;       // number of non-empty particle blocks
-  uint32_t* gflag;      // per grid block: scene+1 if touched this step
-  uint32_t* g_list;     // active grid blocks (arena index)
-  uint32_t* g_scene;    // and owning scene
-  uint32_t* n_g;        // number of active grid blocks
+  uint32_t* gflag;      // per virtual grid block: scene+1 if touched this step
+  uint32_t* table;      // per virtual grid block: pool slot (valid if touched this step)
+  uint32_t* g_list;     // pool slot -> virtual grid block
+  uint32_t* g_scene;    // pool slot -> owning scene
+  uint32_t* n_g;        // number of active grid blocks (may exceed pool_cap on overflow)
+  uint32_t pool_cap;    // pool capacity in blocks
   float4* Gacc;
   float4* Gvel;
   const SceneDev* scenes;

@@ -66,7 +66,7 @@ struct SceneHost {
   bool used = false, alive = false;
   int64_t n = 0;
   int64_t key_base = 0, nkeys = 0;
-  int64_t grid_base = 0, ngb = 0;
+  int64_t table_base = 0, nvb = 0;
   int64_t mat_base = 0, nmat = 0;
   int res = 0;
 };
@@ -91,7 +91,7 @@ struct ckmpm_ctx {
   int device = 0, sm_count = 1;
   ck::LaunchCfg lc{};
 
-  int64_t cap_n = 0, cap_keys = 0, cap_gblocks = 0;
+  int64_t cap_n = 0, cap_keys = 0, cap_vblocks = 0, cap_pool = 0;
   int cap_scenes = 0, cap_mats = 0;
   bool per_E = false;
 
@@ -101,7 +101,7 @@ struct ckmpm_ctx {
   uint32_t* cnt[2]{};
   uint32_t *offset = nullptr, *cursor = nullptr, *perm = nullptr, *pb_key = nullptr, *pb_scene = nullptr;
   uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit)
-  uint32_t *gflag = nullptr, *g_list = nullptr, *g_scene = nullptr;
+  uint32_t *gflag = nullptr, *table = nullptr, *g_list = nullptr, *g_scene = nullptr;
   uint32_t *tile_cnt = nullptr, *tile_ne = nullptr, *scene_tab = nullptr;
   float4 *Gacc = nullptr, *Gvel = nullptr;
   SceneDev* d_scenes = nullptr;
@@ -214,6 +214,8 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.err = ctx->counters + 2;
   v.fp64_count = (unsigned long long*)(ctx->counters + 4);
   v.gflag = ctx->gflag;
+  v.table = ctx->table;
+  v.pool_cap = (uint32_t)ctx->cap_pool;
   v.g_list = ctx->g_list;
   v.g_scene = ctx->g_scene;
   v.Gacc = ctx->Gacc;
@@ -295,7 +297,7 @@ void process_pending(ckmpm_ctx* ctx) {
   for (int slot : ctx->pending_free) {
     SceneHost& s = ctx->scenes[slot];
     ctx->keys_alloc.give(s.key_base, s.nkeys);
-    ctx->grid_alloc.give(s.grid_base, s.ngb);
+    ctx->grid_alloc.give(s.table_base, s.nvb);
     ctx->mat_alloc.give(s.mat_base, s.nmat);
     s = SceneHost{};
   }
@@ -332,6 +334,9 @@ ckmpm_status read_device_error(ckmpm_ctx* ctx) {
     } else if (e & CK_ERR_DOMAIN) {
       ctx->sticky = CKMPM_EDOMAIN;
       ctx->msg = "a particle left the valid interior [0.5 dx, (res-0.5) dx) and was clamped";
+    } else if (e & CK_ERR_POOL) {
+      ctx->sticky = CKMPM_ENOMEM;
+      ctx->msg = "grid pool capacity exceeded: more active grid blocks than max_grid_blocks";
     } else if (e & CK_ERR_INTERNAL) {
       ctx->sticky = CKMPM_EINVAL;
       ctx->msg = "internal consistency check failed (particle outside its block)";
@@ -380,10 +385,12 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
 ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   ctx->kind = cfg->kernel;
   if (ctx->kind != 0 && ctx->kind != 1) return fail(ctx, CKMPM_EINVAL, "kernel must be 0 (CK) or 1 (quadratic)");
-  if (cfg->max_particles < 1 || cfg->max_keys < 1 || cfg->max_grid_blocks < 1 || cfg->max_scenes < 1 ||
+  if (cfg->max_particles < 1 || cfg->max_keys < 1 || cfg->max_grid_blocks < 1 || cfg->max_virtual_blocks < 1 ||
+      cfg->max_scenes < 1 ||
       cfg->max_scenes > 1024 || cfg->max_materials < 1 || cfg->max_materials > 65535)
     return fail(ctx, CKMPM_EINVAL, "invalid capacities");
-  if (cfg->max_particles > 0x7fffffffLL || cfg->max_keys > 0x7fffffffLL || cfg->max_grid_blocks > 0x7fffffffLL)
+  if (cfg->max_particles > 0x7fffffffLL || cfg->max_keys > 0x7fffffffLL || cfg->max_grid_blocks > 0x7fffffffLL ||
+      cfg->max_virtual_blocks > 0x7fffffffLL)
     return fail(ctx, CKMPM_EINVAL, "capacities must be below 2^31");
   if (cfg->allocator) {
     if (!cfg->allocator->alloc || !cfg->allocator->free) return fail(ctx, CKMPM_EINVAL, "allocator needs alloc and free");
@@ -404,7 +411,8 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   ctx->lc.stream = ctx->stream;
   ctx->cap_n = cfg->max_particles;
   ctx->cap_keys = cfg->max_keys;
-  ctx->cap_gblocks = cfg->max_grid_blocks;
+  ctx->cap_pool = cfg->max_grid_blocks;
+  ctx->cap_vblocks = cfg->max_virtual_blocks;
   ctx->cap_scenes = cfg->max_scenes;
   ctx->cap_mats = cfg->max_materials;
   ctx->per_E = cfg->per_particle_E != 0;
@@ -415,26 +423,27 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
             alloc_n(ctx, ctx->cnt[1], ctx->cap_keys) && alloc_n(ctx, ctx->offset, ctx->cap_keys) &&
             alloc_n(ctx, ctx->cursor, ctx->cap_keys) && alloc_n(ctx, ctx->pb_key, ctx->cap_keys) &&
             alloc_n(ctx, ctx->pb_scene, ctx->cap_keys) && alloc_n(ctx, ctx->counters, 8) &&
-            alloc_n(ctx, ctx->gflag, ctx->cap_gblocks) && alloc_n(ctx, ctx->g_list, ctx->cap_gblocks) &&
-            alloc_n(ctx, ctx->g_scene, ctx->cap_gblocks) &&
+            alloc_n(ctx, ctx->gflag, ctx->cap_vblocks) && alloc_n(ctx, ctx->table, ctx->cap_vblocks) &&
+            alloc_n(ctx, ctx->g_list, ctx->cap_pool) && alloc_n(ctx, ctx->g_scene, ctx->cap_pool) &&
             alloc_n(ctx, ctx->tile_cnt, ceil_div(ctx->cap_keys, ck::kScanTile) + 1) &&
             alloc_n(ctx, ctx->tile_ne, ceil_div(ctx->cap_keys, ck::kScanTile) + 1) &&
             alloc_n(ctx, ctx->scene_tab, 2 * (int64_t)ctx->cap_scenes + 2) &&
-            alloc_n(ctx, ctx->Gacc, ctx->cap_gblocks * NG * ck::kBlockNodes) &&
-            alloc_n(ctx, ctx->Gvel, ctx->cap_gblocks * NG * ck::kBlockNodes) &&
+            alloc_n(ctx, ctx->Gacc, ctx->cap_pool * NG * ck::kBlockNodes) &&
+            alloc_n(ctx, ctx->Gvel, ctx->cap_pool * NG * ck::kBlockNodes) &&
             alloc_n(ctx, ctx->d_scenes, ctx->cap_scenes) && alloc_n(ctx, ctx->d_mats, ctx->cap_mats);
   if (!ok) return fail(ctx, CKMPM_ENOMEM, "device memory allocation failed");
   CK_TRY(cudaMemsetAsync(ctx->cnt[0], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->cnt[1], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->counters, 0, sizeof(uint32_t) * 8, ctx->stream), "memset");
-  CK_TRY(cudaMemsetAsync(ctx->gflag, 0, sizeof(uint32_t) * ctx->cap_gblocks, ctx->stream), "memset");
-  CK_TRY(cudaMemsetAsync(ctx->Gacc, 0, sizeof(float4) * ctx->cap_gblocks * NG * ck::kBlockNodes, ctx->stream), "memset");
-  CK_TRY(cudaMemsetAsync(ctx->Gvel, 0, sizeof(float4) * ctx->cap_gblocks * NG * ck::kBlockNodes, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->gflag, 0, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->table, 0xff, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->Gacc, 0, sizeof(float4) * ctx->cap_pool * NG * ck::kBlockNodes, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->Gvel, 0, sizeof(float4) * ctx->cap_pool * NG * ck::kBlockNodes, ctx->stream), "memset");
   ctx->scenes.assign(ctx->cap_scenes, SceneHost{});
   ctx->h_scenes.assign(ctx->cap_scenes, SceneDev{});
   ctx->h_mats.assign(ctx->cap_mats, MatDev{});
   ctx->keys_alloc.init(ctx->cap_keys);
-  ctx->grid_alloc.init(ctx->cap_gblocks);
+  ctx->grid_alloc.init(ctx->cap_vblocks);
   ctx->mat_alloc.init(ctx->cap_mats);
   CK_TRY(cudaEventCreate(&ctx->step_a), "event");
   CK_TRY(cudaEventCreate(&ctx->step_b), "event");
@@ -527,7 +536,7 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "admission is not allowed during stream capture");
   int64_t npb, nb;
   scene_dims(sc->res, npb, nb);
-  const int64_t nkeys = npb * npb * npb, ngb = nb * nb * nb;
+  const int64_t nkeys = npb * npb * npb, nvb = nb * nb * nb;
   if (ctx->n_cur + sc->n > ctx->cap_n) return fail(ctx, CKMPM_ENOMEM, "particle capacity exceeded");
   int slot = -1;
   for (int s = 0; s < ctx->cap_scenes; ++s)
@@ -538,22 +547,22 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   if (slot < 0) return fail(ctx, CKMPM_ENOMEM, "no free scene slot");
   int64_t kb = ctx->keys_alloc.take(nkeys);
   if (kb < 0) return fail(ctx, CKMPM_ENOMEM, "key-space capacity exceeded");
-  int64_t gb = ctx->grid_alloc.take(ngb);
+  int64_t gb = ctx->grid_alloc.take(nvb);
   if (gb < 0) {
     ctx->keys_alloc.give(kb, nkeys);
-    return fail(ctx, CKMPM_ENOMEM, "grid-arena capacity exceeded");
+    return fail(ctx, CKMPM_ENOMEM, "virtual grid-block capacity exceeded");
   }
   int64_t mb = ctx->mat_alloc.take(sc->n_materials);
   if (mb < 0) {
     ctx->keys_alloc.give(kb, nkeys);
-    ctx->grid_alloc.give(gb, ngb);
+    ctx->grid_alloc.give(gb, nvb);
     return fail(ctx, CKMPM_ENOMEM, "material-table capacity exceeded");
   }
   size_t bx = sizeof(float) * 3 * sc->n;
   size_t need = sc->is_device ? 0 : (2 * bx + (size_t)sc->n + 64);
   if (need && !ensure_staging(ctx, need)) {
     ctx->keys_alloc.give(kb, nkeys);
-    ctx->grid_alloc.give(gb, ngb);
+    ctx->grid_alloc.give(gb, nvb);
     ctx->mat_alloc.give(mb, sc->n_materials);
     return fail(ctx, CKMPM_ENOMEM, "staging allocation failed");
   }
@@ -563,8 +572,8 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   h.n = sc->n;
   h.key_base = kb;
   h.nkeys = nkeys;
-  h.grid_base = gb;
-  h.ngb = ngb;
+  h.table_base = gb;
+  h.nvb = nvb;
   h.mat_base = mb;
   h.nmat = sc->n_materials;
   h.res = sc->res;
@@ -581,7 +590,7 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   d.npb = (int)npb;
   d.nb = (int)nb;
   d.key_base = (uint32_t)kb;
-  d.grid_base = gb;
+  d.table_base = gb;
   d.j_tol = (float)sc->fp64_j_tol;
   d.cond_tol = (float)sc->fp64_cond_tol;
   d.gap_tol = (float)sc->fp64_gap_tol;
@@ -704,7 +713,10 @@ ckmpm_status ckmpm_create(const ckmpm_scene* scene, int kernel, void* stream, ck
   cfg.kernel = kernel;
   cfg.max_particles = scene->n;
   cfg.max_keys = npb * npb * npb;
-  cfg.max_grid_blocks = nb * nb * nb;
+  cfg.max_virtual_blocks = nb * nb * nb;
+  // pool for the active blocks: a compact scene at 8 particles per cell
+  // touches about n/512 blocks per grid; n/64 leaves 8x headroom for spreading
+  cfg.max_grid_blocks = std::min<int64_t>(nb * nb * nb, scene->n / 64 + 4096);
   cfg.max_scenes = 1;
   cfg.max_materials = scene->n_materials;
   cfg.per_particle_E = 0;
@@ -798,9 +810,12 @@ ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, 
     out = (float*)tmp;
   }
   if (field >= CKMPM_FIELD_GRID_M) {
-    int64_t n = h.res + 1;
-    ck::launch_read_grid(ctx->kind, ctx->stream, ctx->Gacc, ctx->Gvel, ctx->d_scenes, scene_id,
-                         field - CKMPM_FIELD_GRID_M, out, (long long)NG * n * n * n);
+    cudaError_t me = cudaMemsetAsync(out, 0, want, ctx->stream);
+    if (me != cudaSuccess) {
+      if (tmp) dev_free(ctx, tmp);
+      return cuda_fail(ctx, me, "memset");
+    }
+    ck::launch_read_grid(ctx->kind, ctx->stream, make_view(ctx), scene_id, field - CKMPM_FIELD_GRID_M, out);
   } else {
     const Seg* sg = find_seg(ctx, scene_id);
     if (!sg) {

@@ -21,8 +21,7 @@ void launch_read_particles(int kind, cudaStream_t st, Pool P, const SceneDev* sc
                            uint32_t start, uint32_t n, int field, float* out);
 void launch_write_particles(cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
                             uint32_t start, uint32_t n, int field, const float* in);
-void launch_read_grid(int kind, cudaStream_t st, const float4* Gacc, const float4* Gvel, const SceneDev* scenes,
-                      int scene, int which, float* out, long long total);
+void launch_read_grid(int kind, cudaStream_t st, const StepView& v, int scene, int which, float* out);
 void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene,
                   uint32_t mat_base, uint32_t nmat, uint32_t start, uint32_t n, const float* x, const float* v,
                   const uint8_t* mat, const float* E, uint32_t* err);

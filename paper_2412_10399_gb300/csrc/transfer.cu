@@ -59,12 +59,25 @@ __device__ __forceinline__ void staged_coords(int j, int& slot, int& lx, int& ly
   }
 }
 
-// global arena index of node (ix, iy, iz) of a grid slot in scene s
+// Pool index of a staged node (grid g, local coordinates relative to the
+// particle block's origin 4P) from the pool slots of the 2x2x2 grid blocks
+// the particle block touches; -1 if that block has no slot (pool overflow).
 template <int KIND>
-__device__ __forceinline__ long long arena_index(const SceneDev& s, int slot, int ix, int iy, int iz) {
-  long long gb = s.grid_base + ((long long)(iz >> 2) * s.nb + (iy >> 2)) * s.nb + (ix >> 2);
-  int l = ((iz & 3) * 4 + (iy & 3)) * 4 + (ix & 3);
-  return (gb * Geo<KIND>::NG + slot) * kBlockNodes + l;
+__device__ __forceinline__ long long pool_index(const uint32_t* bslot, int g, int lx, int ly, int lz) {
+  uint32_t sl = bslot[((lz >> 2) * 2 + (ly >> 2)) * 2 + (lx >> 2)];
+  if (sl == CK_NO_SLOT) return -1;
+  int l = ((lz & 3) * 4 + (ly & 3)) * 4 + (lx & 3);
+  return ((long long)sl * Geo<KIND>::NG + g) * kBlockNodes + l;
+}
+
+// Slots of the 2x2x2 grid blocks touched by particle block (bx, by, bz).
+__device__ __forceinline__ void load_block_slots(const StepView& v, const SceneDev& s, int ox, int oy, int oz,
+                                                 uint32_t* bslot) {
+  if (threadIdx.x < 8) {
+    int t = threadIdx.x;
+    int bx = (ox >> 2) + (t & 1), by = (oy >> 2) + ((t >> 1) & 1), bz = (oz >> 2) + (t >> 2);
+    bslot[t] = v.table[s.table_base + ((long long)bz * s.nb + by) * s.nb + bx];
+  }
 }
 
 // ------------------------------------------------------------------ stencils
@@ -209,6 +222,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   __shared__ float sm[4][NS];
+  __shared__ uint32_t bslot[8];
   const uint32_t npb = *v.n_pb;
   for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
     const uint32_t key = v.pb_key[bi];
@@ -217,6 +231,7 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
     const uint32_t cnt = v.cnt_cur[key];
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
+    load_block_slots(v, s, ox, oy, oz, bslot);
     for (int j = threadIdx.x; j < NS; j += blockDim.x) {
       sm[0][j] = 0.f;
       sm[1][j] = 0.f;
@@ -267,10 +282,10 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
     for (int j = threadIdx.x; j < NS; j += blockDim.x) {
       float mm = sm[0][j];
       if (mm != 0.f) {
-        int slot, lx, ly, lz;
-        staged_coords<KIND>(j, slot, lx, ly, lz);
-        long long gi = arena_index<KIND>(s, slot, ox + lx, oy + ly, oz + lz);
-        atomicAdd(&v.Gacc[gi], make_float4(mm, sm[1][j], sm[2][j], sm[3][j]));
+        int g, lx, ly, lz;
+        staged_coords<KIND>(j, g, lx, ly, lz);
+        long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
+        if (gi >= 0) atomicAdd(&v.Gacc[gi], make_float4(mm, sm[1][j], sm[2][j], sm[3][j]));
       }
     }
     __syncthreads();
@@ -285,17 +300,17 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
 template <int KIND>
 __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
   constexpr int NG = Geo<KIND>::NG;
-  const uint32_t ng = *v.n_g;
+  const uint32_t ng = min(*v.n_g, v.pool_cap);
   for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
     const uint32_t g = v.g_list[gi];
     const SceneDev s = v.scenes[v.g_scene[gi]];
-    long long lb = (long long)g - s.grid_base;
+    long long lb = (long long)g - s.table_base;
     int gx = (int)(lb % s.nb), gy = (int)((lb / s.nb) % s.nb), gz = (int)(lb / ((long long)s.nb * s.nb));
     for (int t = threadIdx.x; t < NG * kBlockNodes; t += blockDim.x) {
-      int slot = t / kBlockNodes, l = t % kBlockNodes;
+      int grid = t / kBlockNodes, l = t % kBlockNodes;
       int ix = gx * 4 + (l & 3), iy = gy * 4 + ((l >> 2) & 3), iz = gz * 4 + (l >> 4);
-      float off = KIND == 0 ? (slot == 0 ? 0.25f : -0.25f) : 0.0f;
-      long long idx = ((long long)g * NG + slot) * kBlockNodes + l;
+      float off = KIND == 0 ? (grid == 0 ? 0.25f : -0.25f) : 0.0f;
+      long long idx = ((long long)gi * NG + grid) * kBlockNodes + l;
       float4 acc = v.Gacc[idx];
       float4 o = make_float4(0.f, 0.f, 0.f, acc.x);
       if (acc.x > 0.f) {
@@ -321,6 +336,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   __shared__ float sv[3][NS];
+  __shared__ uint32_t bslot[8];
   const uint32_t npb = *v.n_pb;
   for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
     const uint32_t key = v.pb_key[bi];
@@ -329,13 +345,16 @@ __global__ void __launch_bounds__(128) k_g2p(StepView v) {
     const uint32_t cnt = v.cnt_cur[key];
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
+    load_block_slots(v, s, ox, oy, oz, bslot);
+    __syncthreads();
     for (int j = threadIdx.x; j < NS; j += blockDim.x) {
-      int slot, lx, ly, lz;
-      staged_coords<KIND>(j, slot, lx, ly, lz);
-      float4 g = v.Gvel[arena_index<KIND>(s, slot, ox + lx, oy + ly, oz + lz)];
-      sv[0][j] = g.x;
-      sv[1][j] = g.y;
-      sv[2][j] = g.z;
+      int g, lx, ly, lz;
+      staged_coords<KIND>(j, g, lx, ly, lz);
+      long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
+      float4 gv = gi >= 0 ? v.Gvel[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sv[0][j] = gv.x;
+      sv[1][j] = gv.y;
+      sv[2][j] = gv.z;
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -474,11 +493,10 @@ __global__ void __launch_bounds__(128) k_g2p(StepView v) {
 template <int KIND>
 __global__ void k_clear_gacc(StepView v) {
   constexpr int NG = Geo<KIND>::NG;
-  const uint32_t ng = *v.n_g;
+  const uint32_t ng = min(*v.n_g, v.pool_cap);
   for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
-    const uint32_t g = v.g_list[gi];
     for (int t = threadIdx.x; t < NG * kBlockNodes; t += blockDim.x)
-      v.Gacc[((long long)g * NG + (t / kBlockNodes)) * kBlockNodes + (t % kBlockNodes)] = make_float4(0.f, 0.f, 0.f, 0.f);
+      v.Gacc[((long long)gi * NG + (t / kBlockNodes)) * kBlockNodes + (t % kBlockNodes)] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -612,30 +630,40 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
   }
 }
 
-// Dense grid fields of one scene: out[slot][iz][iy][ix] (x fastest) over
-// 0..res per axis; which: 0 mass, 1 momentum (3), 2 velocity (3).
+// Dense grid fields of one scene: out[grid][iz][iy][ix] (x fastest) over
+// 0..res per axis, written from the active blocks of the last step (the
+// caller zeroes out first); which: 0 mass, 1 momentum (3), 2 velocity (3).
 template <int KIND>
-__global__ void k_read_grid(const float4* Gacc, const float4* Gvel, const SceneDev* scenes, int scene, int which,
+__global__ void k_read_grid(const float4* Gacc, const float4* Gvel, const uint32_t* g_list, const uint32_t* g_scene,
+                            const uint32_t* n_g, uint32_t pool_cap, const SceneDev* scenes, int scene, int which,
                             float* out) {
+  constexpr int NG = Geo<KIND>::NG;
   const SceneDev s = scenes[scene];
   const int n = s.res + 1;
-  const long long total = (long long)Geo<KIND>::NG * n * n * n;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
-    int slot = (int)(q / ((long long)n * n * n));
-    long long r = q % ((long long)n * n * n);
-    int ix = (int)(r % n), iy = (int)((r / n) % n), iz = (int)(r / ((long long)n * n));
-    long long gi = arena_index<KIND>(s, slot, ix, iy, iz);
-    float4 a = Gacc[gi];
-    if (which == 0) {
-      out[q] = a.x;
-    } else if (which == 1) {
-      out[3 * q] = a.y; out[3 * q + 1] = a.z; out[3 * q + 2] = a.w;
-    } else {
-      float4 g = Gvel[gi];
-      bool has = a.x > 0.f;
-      out[3 * q] = has ? g.x : 0.f;
-      out[3 * q + 1] = has ? g.y : 0.f;
-      out[3 * q + 2] = has ? g.z : 0.f;
+  const long long nnode = (long long)n * n * n;
+  const uint32_t ng = min(*n_g, pool_cap);
+  for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+    if ((int)g_scene[gi] != scene) continue;
+    long long lb = (long long)g_list[gi] - s.table_base;
+    int gx = (int)(lb % s.nb), gy = (int)((lb / s.nb) % s.nb), gz = (int)(lb / ((long long)s.nb * s.nb));
+    for (int t = threadIdx.x; t < NG * kBlockNodes; t += blockDim.x) {
+      int grid = t / kBlockNodes, l = t % kBlockNodes;
+      int ix = gx * 4 + (l & 3), iy = gy * 4 + ((l >> 2) & 3), iz = gz * 4 + (l >> 4);
+      if (ix >= n || iy >= n || iz >= n) continue;
+      long long q = grid * nnode + ((long long)iz * n + iy) * n + ix;
+      long long idx = ((long long)gi * NG + grid) * kBlockNodes + l;
+      float4 a = Gacc[idx];
+      if (which == 0) {
+        out[q] = a.x;
+      } else if (which == 1) {
+        out[3 * q] = a.y; out[3 * q + 1] = a.z; out[3 * q + 2] = a.w;
+      } else {
+        float4 g = Gvel[idx];
+        bool has = a.x > 0.f;
+        out[3 * q] = has ? g.x : 0.f;
+        out[3 * q + 1] = has ? g.y : 0.f;
+        out[3 * q + 2] = has ? g.z : 0.f;
+      }
     }
   }
 }
@@ -751,15 +779,13 @@ void launch_write_particles(cudaStream_t st, Pool P, const SceneDev* scenes, con
   k_write_particles<<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, in);
 }
 
-void launch_read_grid(int kind, cudaStream_t st, const float4* Gacc, const float4* Gvel, const SceneDev* scenes,
-                      int scene, int which, float* out, long long total) {
-  int blocks = (int)((total + 255) / 256);
-  if (blocks < 1) blocks = 1;
-  if (blocks > 8192) blocks = 8192;
+void launch_read_grid(int kind, cudaStream_t st, const StepView& v, int scene, int which, float* out) {
   if (kind == 0)
-    k_read_grid<0><<<blocks, 256, 0, st>>>(Gacc, Gvel, scenes, scene, which, out);
+    k_read_grid<0><<<1024, 128, 0, st>>>(v.Gacc, v.Gvel, v.g_list, v.g_scene, v.n_g, v.pool_cap, v.scenes, scene,
+                                          which, out);
   else
-    k_read_grid<1><<<blocks, 256, 0, st>>>(Gacc, Gvel, scenes, scene, which, out);
+    k_read_grid<1><<<1024, 128, 0, st>>>(v.Gacc, v.Gvel, v.g_list, v.g_scene, v.n_g, v.pool_cap, v.scenes, scene,
+                                          which, out);
 }
 
 void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene,

@@ -45,6 +45,7 @@ struct SceneDev {
   uint32_t key_base;  // first particle-block key of this scene
   long long table_base;  // first entry of this scene's block table
   float j_tol, cond_tol, gap_tol;  // float64 SVD criteria
+  float mmax;         // largest particle mass of the scene's materials
   int alive;
 };
 

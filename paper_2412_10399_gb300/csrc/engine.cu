@@ -596,6 +596,9 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   d.gap_tol = (float)sc->fp64_gap_tol;
   d.alive = 1;
   const double V0 = sc->dx * sc->dx * sc->dx / sc->ppc;
+  double mmax = 0.0;
+  for (int i = 0; i < sc->n_materials; ++i) mmax = std::max(mmax, sc->materials[i].rho * V0);
+  d.mmax = (float)mmax;
   for (int i = 0; i < sc->n_materials; ++i) {
     const ckmpm_material& m = sc->materials[i];
     MatDev& md = ctx->h_mats[mb + i];

@@ -5,9 +5,11 @@
 // Teran and Sifakis, "Computing the Singular Value Decomposition of 3x3
 // matrices with minimal branching and elementary floating point operations"
 // (UW-Madison TR1690, 2011): a symmetric cyclic Jacobi eigen-sweep on F^T F
-// gives V, then a Givens QR of F V gives U and the singular values.  The
-// Jacobi rotations here are the exact textbook ones (tan from the smaller root
-// of t^2 + 2 theta t - 1 = 0), not the paper's approximate quaternion Givens.
+// gives V, then a Givens QR of F V gives U and the singular values.  Each
+// Jacobi rotation is exact (it zeroes its off-diagonal), with its angle taken
+// from the half-angle identities cos^2(phi) = (1 + cos 2phi)/2,
+// sin(phi) = sin(2phi) / (2 cos phi), so that it needs two reciprocal square
+// roots and no division; the angle is kept in [-pi/4, pi/4].
 // The result is rotation-variant: det U = det V = +1, sigma_0 >= sigma_1 >= 0
 // and sigma_2 carries the sign of det F.
 #pragma once
@@ -20,13 +22,15 @@ struct Num;
 template <>
 struct Num<float> {
   __device__ static __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-  __device__ static __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+  // reciprocal square root refined by one Newton step y <- y (3 - x y^2) / 2
+  __device__ static __forceinline__ float rsqrt_(float x) {
+    float y = rsqrtf(x);
+    return y * (1.5f - 0.5f * x * y * y);
+  }
   __device__ static __forceinline__ float abs_(float x) { return fabsf(x); }
   __device__ static __forceinline__ float log_(float x) { return logf(x); }
   __device__ static __forceinline__ float exp_(float x) { return expf(x); }
-  __device__ static __forceinline__ float hypot_(float a, float b) { return hypotf(a, b); }
-  static constexpr int sweeps = 5;
-  static constexpr float huge_theta = 1e15f;
+  static constexpr int sweeps = 4;
   static constexpr float eps = 5.9604645e-8f;  // 2^-24
 };
 template <>
@@ -36,9 +40,7 @@ struct Num<double> {
   __device__ static __forceinline__ double abs_(double x) { return fabs(x); }
   __device__ static __forceinline__ double log_(double x) { return log(x); }
   __device__ static __forceinline__ double exp_(double x) { return exp(x); }
-  __device__ static __forceinline__ double hypot_(double a, double b) { return hypot(a, b); }
-  static constexpr int sweeps = 8;
-  static constexpr double huge_theta = 1e150;
+  static constexpr int sweeps = 6;
   static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
 };
 
@@ -51,25 +53,28 @@ struct Num<double> {
 // rotation's c and s and puts an ulp of noise into the singular values.
 template <typename T>
 __device__ __forceinline__ void jacobi_rotate(T* S, T* V, int p, int q, int r) {
-  T apq = CK_M(S, p, q);
-  if (Num<T>::abs_(apq) <= Num<T>::eps * (Num<T>::abs_(CK_M(S, p, p)) + Num<T>::abs_(CK_M(S, q, q)))) {
+  const T apq = CK_M(S, p, q), spp = CK_M(S, p, p), sqq = CK_M(S, q, q);
+  if (Num<T>::abs_(apq) <= Num<T>::eps * (Num<T>::abs_(spp) + Num<T>::abs_(sqq))) {
     CK_M(S, p, q) = T(0);
     CK_M(S, q, p) = T(0);
     return;
   }
-  T theta = (CK_M(S, q, q) - CK_M(S, p, p)) / (T(2) * apq);
-  T at = Num<T>::abs_(theta);
-  T t = at > Num<T>::huge_theta ? T(0.5) / theta
-                                : (theta >= T(0) ? T(1) : T(-1)) / (at + Num<T>::sqrt_(theta * theta + T(1)));
-  T c = Num<T>::rsqrt_(t * t + T(1));
-  T s = t * c;
-  T spp = CK_M(S, p, p) - t * apq;
-  T sqq = CK_M(S, q, q) + t * apq;
-  T srp = CK_M(S, r, p), srq = CK_M(S, r, q);
-  T nrp = c * srp - s * srq;
-  T nrq = s * srp + c * srq;
-  CK_M(S, p, p) = spp;
-  CK_M(S, q, q) = sqq;
+  // S' = J^T S J, J = [[c, s], [-s, c]] in the (p, q) plane; S'_pq = 0 needs
+  // cos(2phi) S_pq + sin(2phi) (S_pp - S_qq) / 2 = 0.
+  const T x = spp - sqq, y = T(2) * apq;
+  const T ir = Num<T>::rsqrt_(x * x + y * y);
+  const T c2 = Num<T>::abs_(x) * ir;            // cos 2phi >= 0
+  const T s2 = (x >= T(0) ? -y : y) * ir;      // sin 2phi
+  const T h = T(0.5) + T(0.5) * c2;            // cos^2 phi in [1/2, 1]
+  const T rh = Num<T>::rsqrt_(h);
+  const T c = h * rh;
+  const T s = T(0.5) * s2 * rh;
+  const T cc = c * c, ss = s * s, cs2 = T(2) * c * s;
+  const T srp = CK_M(S, r, p), srq = CK_M(S, r, q);
+  const T nrp = c * srp - s * srq;
+  const T nrq = s * srp + c * srq;
+  CK_M(S, p, p) = cc * spp - cs2 * apq + ss * sqq;
+  CK_M(S, q, q) = ss * spp + cs2 * apq + cc * sqq;
   CK_M(S, p, q) = T(0);
   CK_M(S, q, p) = T(0);
   CK_M(S, r, p) = nrp;
@@ -100,13 +105,16 @@ __device__ __forceinline__ void swap_cols_neg(T* V, T* e, int a, int b) {
 
 template <typename T>
 __device__ __forceinline__ void givens_rows(T* Bm, T* U, int p, int q) {
-  // zero Bm[q][p] by rotating rows p and q; accumulate U <- U G^T
-  T a = CK_M(Bm, p, p), b = CK_M(Bm, q, p);
-  T r = Num<T>::hypot_(a, b);
-  T c = T(1), s = T(0);
-  if (r > T(0)) {
-    c = a / r;
-    s = b / r;
+  // zero Bm[q][p] by rotating rows p and q (Bm[p][p] ends >= 0); U <- U G^T
+  const T a = CK_M(Bm, p, p), b = CK_M(Bm, q, p);
+  T c, s;
+  if (b == T(0)) {
+    c = a >= T(0) ? T(1) : T(-1);
+    s = T(0);
+  } else {
+    const T ir = Num<T>::rsqrt_(a * a + b * b);
+    c = a * ir;
+    s = b * ir;
   }
 #pragma unroll
   for (int j = 0; j < 3; ++j) {

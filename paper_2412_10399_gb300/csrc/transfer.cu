@@ -218,12 +218,26 @@ __device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, in
 
 // ------------------------------------------------------------------------ P2G
 
+// Shared-memory accumulation is in 32-bit fixed point: integer shared
+// atomics run about 4x faster than float ones on this part, and integer sums
+// do not depend on the order of the atomics.  A first pass over the block's
+// particles bounds every contribution (|w| <= 1, |x_i - x_p| <= 2 cells,
+// |D^-1| <= 12.5 cells^-2 for both stencils; the smallest eigenvalue of the
+// CK D is 0.0826 cells^2), so with cnt particles no node sum can exceed
+// cnt * bound; the scale maps that to 2^30 (no overflow).  Mass uses one
+// integer; each momentum component is split into a high part (the rounded
+// scaled value) and a low part (the rounding remainder times 2^16), so the
+// sum keeps float precision however loose the bound is.
+constexpr float kDinvBound = 12.5f;
+
 template <int KIND>
 __global__ void __launch_bounds__(128) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  __shared__ float sm[4][NS];
+  __shared__ int sm[7][NS];
   __shared__ uint32_t bslot[8];
+  __shared__ float sred[2][4];
   const uint32_t npb = *v.n_pb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
@@ -233,17 +247,41 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
     for (int j = threadIdx.x; j < NS; j += blockDim.x) {
-      sm[0][j] = 0.f;
-      sm[1][j] = 0.f;
-      sm[2][j] = 0.f;
-      sm[3][j] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 7; ++c) sm[c][j] = 0;
+    }
+    // pass 1: bounds of |m v| and of the affine term over the block
+    float bv = 0.f, bm = 0.f;
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const uint32_t p = v.perm[start + i];
+      const float4 a = v.cur.VM0[p];
+      const float4 b = v.cur.VM1[p];
+      const float4 c = v.cur.VM2[p];
+      bv = fmaxf(bv, fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))));
+      float r0 = fabsf(a.w) + fabsf(b.x) + fabsf(b.y);
+      float r1 = fabsf(b.z) + fabsf(b.w) + fabsf(c.x);
+      float r2 = fabsf(c.y) + fabsf(c.z) + fabsf(c.w);
+      bm = fmaxf(bm, fmaxf(r0, fmaxf(r1, r2)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      bv = fmaxf(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+      bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    }
+    if (lane == 0) {
+      sred[0][warp] = bv;
+      sred[1][warp] = bm;
     }
     __syncthreads();
-    // Lanes of a warp take particles C = ceil(cnt/32) apart in the block's
-    // order.  Particles of one cell sit next to each other (sampling order,
-    // kept by the binning), so neighbouring lanes come from different cells
-    // and their shared-memory atomics hit different nodes instead of
-    // serialising on the same address.
+    bv = fmaxf(fmaxf(sred[0][0], sred[0][1]), fmaxf(sred[0][2], sred[0][3]));
+    bm = fmaxf(fmaxf(sred[1][0], sred[1][1]), fmaxf(sred[1][2], sred[1][3]));
+    const float fcnt = (float)cnt;
+    const float bound_p = s.mmax * bv + 2.0f * 3.0f * kDinvBound * bm * s.inv_dx;
+    const float Sm = 1073741824.0f / (fcnt * s.mmax);
+    const float Sp = bound_p > 0.f ? 1073741824.0f / (fcnt * bound_p) : 1.0f;
+    // pass 2: lanes of a warp take particles C = ceil(cnt/32) apart in the
+    // block's order; particles of one cell sit next to each other (sampling
+    // order, kept by the binning), so neighbouring lanes come from different
+    // cells and their atomics hit different nodes instead of serialising.
     const uint32_t C = (cnt + 31u) >> 5;
     for (uint32_t q = threadIdx.x; q < (C << 5); q += blockDim.x) {
       const uint32_t i = (q & 31u) * C + (q >> 5);
@@ -262,30 +300,46 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
       float Di[9];
       dinv_of<KIND>(st, Di);
       const float M[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-      // A^ = M D^-1 / dx so that A (x_i - x_p) = A^ (offset in cells)
+      // A^ = M D^-1 / dx so that A (x_i - x_p) = A^ (offset in cells), pre-scaled
       float A[9];
+      const float ks = s.inv_dx * Sp;
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-          A[r * 3 + q] = (M[r * 3 + 0] * Di[0 * 3 + q] + M[r * 3 + 1] * Di[1 * 3 + q] + M[r * 3 + 2] * Di[2 * 3 + q]) * s.inv_dx;
+        for (int qq = 0; qq < 3; ++qq)
+          A[r * 3 + qq] = (M[r * 3 + 0] * Di[0 * 3 + qq] + M[r * 3 + 1] * Di[1 * 3 + qq] + M[r * 3 + 2] * Di[2 * 3 + qq]) * ks;
       const float m = mt.mass;
-      const float px = m * a.x, py = m * a.y, pz = m * a.z;
+      const float ms = m * Sm;
+      const float px = m * a.x * Sp, py = m * a.y * Sp, pz = m * a.z * Sp;
       for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
-        atomicAdd(&sm[0][j], w * m);
-        atomicAdd(&sm[1][j], w * (px + A[0] * dx + A[1] * dy + A[2] * dz));
-        atomicAdd(&sm[2][j], w * (py + A[3] * dx + A[4] * dy + A[5] * dz));
-        atomicAdd(&sm[3][j], w * (pz + A[6] * dx + A[7] * dy + A[8] * dz));
+        atomicAdd(&sm[0][j], __float2int_rn(w * ms));
+        const float vx = w * (px + A[0] * dx + A[1] * dy + A[2] * dz);
+        const float vy = w * (py + A[3] * dx + A[4] * dy + A[5] * dz);
+        const float vz = w * (pz + A[6] * dx + A[7] * dy + A[8] * dz);
+        const float hx = rintf(vx), hy = rintf(vy), hz = rintf(vz);
+        atomicAdd(&sm[1][j], (int)hx);
+        atomicAdd(&sm[2][j], __float2int_rn((vx - hx) * 65536.0f));
+        atomicAdd(&sm[3][j], (int)hy);
+        atomicAdd(&sm[4][j], __float2int_rn((vy - hy) * 65536.0f));
+        atomicAdd(&sm[5][j], (int)hz);
+        atomicAdd(&sm[6][j], __float2int_rn((vz - hz) * 65536.0f));
       });
     }
     __syncthreads();
+    const float iSm = 1.0f / Sm, iSp = 1.0f / Sp;
     for (int j = threadIdx.x; j < NS; j += blockDim.x) {
-      float mm = sm[0][j];
-      if (mm != 0.f) {
+      int mi = sm[0][j];
+      if (mi != 0) {
         int g, lx, ly, lz;
         staged_coords<KIND>(j, g, lx, ly, lz);
         long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
-        if (gi >= 0) atomicAdd(&v.Gacc[gi], make_float4(mm, sm[1][j], sm[2][j], sm[3][j]));
+        if (gi >= 0) {
+          const float l16 = 1.0f / 65536.0f;
+          float4 o = make_float4((float)mi * iSm, ((float)sm[1][j] + (float)sm[2][j] * l16) * iSp,
+                                 ((float)sm[3][j] + (float)sm[4][j] * l16) * iSp,
+                                 ((float)sm[5][j] + (float)sm[6][j] * l16) * iSp);
+          atomicAdd(&v.Gacc[gi], o);
+        }
       }
     }
     __syncthreads();
@@ -333,7 +387,7 @@ __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
 __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(a, fminf(b, c)); }
 
 template <int KIND>
-__global__ void __launch_bounds__(128) k_g2p(StepView v) {
+__global__ void __launch_bounds__(128, 4) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   __shared__ float sv[3][NS];
   __shared__ uint32_t bslot[8];

@@ -204,6 +204,33 @@ CKMPM_API ckmpm_status ckmpm_destroy(ckmpm_ctx* ctx);
 /* Human-readable description of the last error of ctx (never NULL). */
 CKMPM_API const char* ckmpm_last_error(const ckmpm_ctx* ctx);
 
+/* Allocation-free variant of the particle-to-grid transfer (no counterpart in
+ * the paper; it exists for callers that may not allocate device memory when
+ * they call: an application whose own fixed arena owns the device memory, a
+ * real-time loop that cannot afford cudaMalloc's implicit synchronisation, or
+ * a plug-in that must not grow the process's footprint after start-up).
+ *
+ * Computes for one scene the same grids as ckmpm_create + ckmpm_upload(F, B)
+ * + ckmpm_probe_grids + ckmpm_readback(GRID_M, GRID_P): mass and momentum
+ * (m v + dt f) of both CK grids (or the quadratic grid) after P2G.  It calls
+ * no cudaMalloc, cudaFree or allocating library routine: all working memory is
+ * one fixed 18 MiB device array inside the library, held on every GPU that
+ * loads the library until the process exits.
+ *   scene   is_device must be 1 (x, v, mat already on the current device);
+ *           n <= 65536, res <= 64, n_materials <= 16, else CKMPM_EINVAL.
+ *   kernel  ckmpm_kernel.
+ *   B, F    device arrays of n*9 floats (row-major) or NULL (B = 0, F = I).
+ *   grid_m  device output, (res+1)^3 floats per grid (G- then G+ for CK).
+ *   grid_p  device output, (res+1)^3 * 3 floats per grid.
+ *   stream  cudaStream_t or NULL; the call returns after the work finished.
+ * Every call on a GPU shares that array (a previous call's leftovers are
+ * cleared first), so calls that overlap on the same GPU race.  The first call
+ * on each GPU looks up the array's address with that GPU current: make it
+ * before any stream capture.  Returns EDOMAIN / ENONFINITE for particles
+ * outside the interior or non-finite input, ECUDA on a runtime error. */
+CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* scene, int kernel, const float* B,
+                                             const float* F, float* grid_m, float* grid_p, void* stream);
+
 /* Library version string. */
 CKMPM_API const char* ckmpm_version(void);
 

@@ -83,6 +83,7 @@ SIGNATURES = {
     "ckmpm_destroy": (ctypes.c_int, [_P]),
     "ckmpm_last_error": (ctypes.c_char_p, [_P]),
     "ckmpm_version": (ctypes.c_char_p, []),
+    "ckmpm_p2g_grids_static": (ctypes.c_int, [ctypes.POINTER(ckmpm_scene), ctypes.c_int, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -190,6 +191,13 @@ def ckmpm_destroy(ctx):
 
 def ckmpm_last_error(ctx) -> str:
     return load().ckmpm_last_error(ctx).decode()
+
+
+def ckmpm_p2g_grids_static(scene: ckmpm_scene, kernel: int, B_ptr: int, F_ptr: int, grid_m_ptr: int,
+                           grid_p_ptr: int, stream: int = 0):
+    """Allocation-free P2G into caller-provided device grids (see the C header)."""
+    _check(load().ckmpm_p2g_grids_static(ctypes.byref(scene), kernel, _P(B_ptr or None), _P(F_ptr or None),
+                                         _P(grid_m_ptr), _P(grid_p_ptr), _P(stream or None)))
 
 
 # ------------------------------------------------------------ marshalling helpers

@@ -59,13 +59,16 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("common.cuh", "launch.h", "svd3.cuh", "transfer.cu")
+
+
 def _source_hash():
+    """Hash of the sources that define the P2G / grid / G2P kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2412_10399_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(f.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

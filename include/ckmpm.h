@@ -204,6 +204,41 @@ CKMPM_API ckmpm_status ckmpm_destroy(ckmpm_ctx* ctx);
 /* Human-readable description of the last error of ctx (never NULL). */
 CKMPM_API const char* ckmpm_last_error(const ckmpm_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Differentiable stepper (extension: gradients of a rollout).
+ *
+ * One CK-MPM step (Sec. 4.3-4.5 with readings R4-R8) as a pure function of the
+ * particle state, for the fixed-corotated model, on a dense dual grid of
+ * (res+1)^3 nodes per grid, with particles kept in the caller's order; and its
+ * adjoint (reverse of G2P, grid update and P2G, including the derivatives of
+ * the kernel weights, of D(x) and of the polar decomposition).  All state
+ * arrays are float32 device arrays owned by the caller: x, v n*3; B, F n*9
+ * (row-major 3x3); E n (per-particle Young's modulus).  Work is enqueued on the
+ * stream given at creation; ckmpm_diff_sync waits and reports EDOMAIN if a
+ * particle touched nodes outside 0..res.
+ * ------------------------------------------------------------------------- */
+typedef struct ckmpm_diff ckmpm_diff;
+
+/* scene: n, res, dx, dt, gravity, bc_cells, ppc and materials[0] (must be
+ * fixed-corotated; its rho and nu are used, E comes per particle).  Device
+ * buffers for the dense grids are allocated here.  EINVAL / ENOMEM. */
+CKMPM_API ckmpm_status ckmpm_diff_create(const ckmpm_scene* scene, void* stream, ckmpm_diff** out);
+
+/* (x, v, B, F; E) -> (x1, v1, B1, F1); outputs must not alias inputs. */
+CKMPM_API ckmpm_status ckmpm_diff_step(ckmpm_diff* d, const float* x, const float* v, const float* B,
+                                       const float* F, const float* E, float* x1, float* v1, float* B1, float* F1);
+
+/* Vector-Jacobian product of one step at (x, v, B, F; E): given the adjoints
+ * (gx1, gv1, gB1, gF1) of the step's outputs, writes the adjoints (gx, gv,
+ * gB, gF) of its inputs and ADDS d<adjoint, step>/dE to gE. */
+CKMPM_API ckmpm_status ckmpm_diff_step_backward(ckmpm_diff* d, const float* x, const float* v, const float* B,
+                                                const float* F, const float* E, const float* gx1, const float* gv1,
+                                                const float* gB1, const float* gF1, float* gx, float* gv, float* gB,
+                                                float* gF, float* gE);
+
+CKMPM_API ckmpm_status ckmpm_diff_sync(ckmpm_diff* d);
+CKMPM_API ckmpm_status ckmpm_diff_destroy(ckmpm_diff* d);
+
 /* Allocation-free variant of the particle-to-grid transfer (no counterpart in
  * the paper; it exists for callers that may not allocate device memory when
  * they call: an application whose own fixed arena owns the device memory, a

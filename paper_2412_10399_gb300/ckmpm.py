@@ -84,6 +84,11 @@ SIGNATURES = {
     "ckmpm_last_error": (ctypes.c_char_p, [_P]),
     "ckmpm_version": (ctypes.c_char_p, []),
     "ckmpm_p2g_grids_static": (ctypes.c_int, [ctypes.POINTER(ckmpm_scene), ctypes.c_int, _P, _P, _P, _P, _P]),
+    "ckmpm_diff_create": (ctypes.c_int, [ctypes.POINTER(ckmpm_scene), _P, ctypes.POINTER(_P)]),
+    "ckmpm_diff_step": (ctypes.c_int, [_P] + [_P] * 9),
+    "ckmpm_diff_step_backward": (ctypes.c_int, [_P] + [_P] * 14),
+    "ckmpm_diff_sync": (ctypes.c_int, [_P]),
+    "ckmpm_diff_destroy": (ctypes.c_int, [_P]),
 }
 
 _lib = None

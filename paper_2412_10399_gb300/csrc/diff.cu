@@ -289,8 +289,16 @@ __global__ void k_fwd_g2p(DP p, const float* x, const float* F, const float* gv,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
     DS s;
     s.set(p, x[3 * i], x[3 * i + 1], x[3 * i + 2]);
-    if (!nodes_in_range(p, s)) {
+    if (!nodes_in_range(p, s)) {  // reported by ckmpm_diff_sync; the particle is left in place
       atomicOr(err, 1u);
+      for (int q = 0; q < 9; ++q) {
+        if (q < 3) {
+          x1[3 * i + q] = x[3 * i + q];
+          v1[3 * i + q] = 0.f;
+        }
+        B1[9 * i + q] = 0.f;
+        F1[9 * i + q] = F[9 * i + q];
+      }
       continue;
     }
     float vv[3] = {0.f, 0.f, 0.f}, Bh[9] = {0.f};
@@ -346,7 +354,13 @@ __global__ void k_bwd_g2p(DP p, const float* x, const float* F, const float* gv,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
     DS s;
     s.set(p, x[3 * i], x[3 * i + 1], x[3 * i + 2]);
-    if (!nodes_in_range(p, s)) continue;
+    if (!nodes_in_range(p, s)) {
+      for (int q = 0; q < 9; ++q) {
+        if (q < 3) gx[3 * i + q] = 0.f;
+        gF[9 * i + q] = 0.f;
+      }
+      continue;
+    }
     // recompute the forward gather
     float vv[3] = {0.f, 0.f, 0.f}, Bh[9] = {0.f};
     for (int g = 0; g < 2; ++g)
@@ -444,7 +458,13 @@ __global__ void k_bwd_p2g(DP p, const float* x, const float* v, const float* B, 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gridDim.x * blockDim.x) {
     DS s;
     s.set(p, x[3 * i], x[3 * i + 1], x[3 * i + 2]);
-    if (!nodes_in_range(p, s)) continue;
+    if (!nodes_in_range(p, s)) {
+      for (int q = 0; q < 9; ++q) {
+        if (q < 3) gv[3 * i + q] = 0.f;
+        gB[9 * i + q] = 0.f;
+      }
+      continue;
+    }
     float Fi[9], Bi[9], tau[9], U[9], V[9], sig[3], mu, lam;
     load9(F, i, Fi);
     load9(B, i, Bi);

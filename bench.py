@@ -222,76 +222,26 @@ def _time_steps(ck, ctx, steps, stream_ptr):
     return a.elapsed_time(b)
 
 
-def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0):
-    """Continuous batching of a Poisson stream of scenes in one context: each
-    global step advances every resident scene; arrivals are admitted between
-    steps as capacity allows; completed scenes are released.  Returns p50/p99
-    of the per-scene step latency (the device time of the global step each
-    scene step belonged to) and the aggregate particle-steps/s."""
-    import torch
+def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0, budget_bytes=1 << 30):
+    """Continuous batching of a Poisson stream of scenes through the serving
+    loop: admission by a device-memory budget, one launch per kernel per
+    global step over every resident scene, retirement with readback."""
     from paper_2412_10399_gb300 import scenes as S
+    from paper_2412_10399_gb300 import serving as SV
     reqs = S.served_mix(n_scenes=n_scenes, seed=seed, n_max=2e6 * scale, steps=steps)
-    cap_n = int(sum(r.scene.n for r in reqs) * 0.6) + 1
-    nb = (128 // 4 + 1) ** 3
-    cfg = ck.ckmpm_config()
-    cfg.kernel = ck.KERNEL_CK
-    cfg.max_particles = cap_n
-    cfg.max_keys = (128 // 4) ** 3 * 8
-    cfg.max_virtual_blocks = nb * 8
-    cfg.max_grid_blocks = cap_n // 64 + 8 * 4096
-    cfg.max_scenes = 8
-    cfg.max_materials = 64
-    cfg.stream = stream_ptr
-    ctx = ck.ckmpm_create_server(cfg)
-    stream = torch.cuda.ExternalStream(stream_ptr)
-    pending = list(reqs)
-    resident = {}  # scene id -> [remaining steps, n, keep]
-    lat = []
-    total_ps = 0
-    t_start = time.perf_counter()
-    wall0 = time.perf_counter()
-    busy_ms = 0.0
-    while pending or resident:
-        now = time.perf_counter() - t_start
-        while pending and pending[0].arrival_s * 0.05 <= now:
-            r = pending[0]
-            sc, keep = ck.scene_struct(r.scene)
-            try:
-                sid = ck.ckmpm_admit(ctx, sc)
-            except ck.CKMPMError as e:
-                if e.status == ck.ENOMEM:
-                    break
-                raise
-            resident[sid] = [r.scene.steps, r.scene.n, keep]
-            pending.pop(0)
-        if not resident:
-            time.sleep(0.001)
-            continue
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ck.ckmpm_step(ctx, 1)
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b)
-        busy_ms += ms
-        for sid in list(resident):
-            lat.append(ms)
-            total_ps += resident[sid][1]
-            resident[sid][0] -= 1
-            if resident[sid][0] == 0:
-                ck.ckmpm_release(ctx, sid)
-                del resident[sid]
-    ck.ckmpm_sync(ctx)
-    wall = time.perf_counter() - wall0
-    ck.ckmpm_destroy(ctx)
-    lat.sort()
-    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "scene_steps": len(lat), "scenes": n_scenes, "steps_per_scene": steps,
-            "aggregate_particle_steps_per_s": total_ps / (busy_ms / 1e3),
-            "wall_particle_steps_per_s": total_ps / wall,
-            "mix": f"{n_scenes} scenes, N log-uniform in [1e4, {2e6 * scale:.0f}], box/sphere, elastic or sand, "
-                   f"{steps} steps each, arrivals Poisson (20 ms mean, time-compressed x20)"}
+    budget = SV.Budget.from_bytes(budget_bytes, max_res=128, max_scenes=6)
+    eng = SV.EngineCK(budget, stream=stream_ptr)
+    srv = SV.Server(eng, budget)
+    for r in reqs:
+        srv.submit(SV.Request(r.scene, r.scene.steps, arrival_s=r.arrival_s * 0.05, read_fields=(ck.FIELD_X,)))
+    srv.run()
+    st = srv.stats()
+    eng.close()
+    st.update({"scenes": n_scenes, "steps_per_scene": steps, "budget_bytes": budget_bytes,
+               "mix": f"{n_scenes} scenes, N log-uniform in [1e4, {2e6 * scale:.0f}], box/sphere, elastic or "
+                      f"sand, {steps} steps each, Poisson arrivals (20 ms mean, time-compressed x20), "
+                      f"admitted under a {budget_bytes >> 20} MiB device budget"})
+    return st
 
 
 def run_gpu(args):

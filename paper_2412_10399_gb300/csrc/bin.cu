@@ -216,6 +216,20 @@ __global__ void k_glist(StepView v, uint32_t n_vblocks) {
   }
 }
 
+// Retire particles [start, start + n) of the current pool (a released scene):
+// they get the dead key and leave the pool at the next step.
+__global__ void k_mark_dead(uint32_t* key, uint32_t start, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    key[start + i] = CK_DEAD_KEY;
+}
+
+void launch_mark_dead(cudaStream_t st, uint32_t* key, uint32_t start, uint32_t n) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  k_mark_dead<<<blocks, 256, 0, st>>>(key, start, n);
+}
+
 void launch_bin(cudaStream_t st, const StepView& v, const BinScratch& bs, int which, uint32_t n_gblocks,
                 int grid_ctas) {
   uint32_t ntiles = (v.n_keys + kScanTile - 1) / kScanTile;

@@ -747,14 +747,28 @@ ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id) {
   if (scene_id < 0 || scene_id >= ctx->cap_scenes || !ctx->scenes[scene_id].alive)
     return fail(ctx, CKMPM_ENOTFOUND, "unknown scene id");
   if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "release is not allowed during stream capture");
-  ctx->scenes[scene_id].alive = false;
+  SceneHost& h = ctx->scenes[scene_id];
+  // retire its particles now (dead keys, cleared histogram range) so that its
+  // slot, key range, block table and materials can be reused at once; the
+  // particles themselves leave the pool at the next step
+  for (size_t i = 0; i < ctx->layout.size(); ++i) {
+    if (ctx->layout[i].slot == scene_id) {
+      ck::launch_mark_dead(ctx->stream, ctx->key[ctx->cur], (uint32_t)ctx->layout[i].start,
+                           (uint32_t)ctx->layout[i].n);
+      ctx->layout.erase(ctx->layout.begin() + i);
+      break;
+    }
+  }
+  CK_TRY(cudaMemsetAsync(ctx->cnt[ctx->cur] + h.key_base, 0, sizeof(uint32_t) * h.nkeys, ctx->stream), "memset");
+  h.alive = false;
   ctx->h_scenes[scene_id].alive = 0;
   CK_TRY(cudaMemcpyAsync(ctx->d_scenes + scene_id, &ctx->h_scenes[scene_id], sizeof(SceneDev), cudaMemcpyHostToDevice,
                          ctx->stream),
          "upload scene");
   upload_scene_tab(ctx);
-  ctx->keys_dirty = true;
   ctx->pending_free.push_back(scene_id);
+  process_pending(ctx);
+  CK_TRY(cudaGetLastError(), "release");
   return CKMPM_OK;
 }
 

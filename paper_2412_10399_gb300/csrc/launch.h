@@ -39,5 +39,6 @@ struct BinScratch {
 void launch_bin(cudaStream_t st, const StepView& v, const BinScratch& bs, int which, uint32_t n_gblocks,
                 int grid_ctas);
 enum { LB_SCAN_TILES = 0, LB_SCAN_TOP = 1, LB_SCAN_FINAL = 2, LB_SCATTER = 3, LB_GLIST = 4 };
+void launch_mark_dead(cudaStream_t st, uint32_t* key, uint32_t start, uint32_t n);
 
 }  // namespace ck

@@ -765,12 +765,13 @@ __global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* sc
 }
 
 // Recompute keys and the histogram of the whole current pool (after an
-// upload of positions or a release); particles of released scenes get the
-// dead key and leave the pool at the next step.
+// upload of positions); particles already retired by a release keep the dead
+// key and leave the pool at the next step.
 template <int KIND>
 __global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, const MatDev* mats, uint32_t n,
                         uint32_t* err) {
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    if (key[t] == CK_DEAD_KEY) continue;  // retired by a release; its slot may already be reused
     float4 X = P.X[t];
     const MatDev mt = mats[__float_as_uint(X.w)];
     const SceneDev s = scenes[mt.scene];

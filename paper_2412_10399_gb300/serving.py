@@ -111,7 +111,12 @@ class EngineCK:
 
     def admit(self, scene) -> int:
         sc, keep = self.ck.scene_struct(scene)
-        return self.ck.ckmpm_admit(self.ctx, sc)
+        try:
+            return self.ck.ckmpm_admit(self.ctx, sc)
+        except self.ck.CKMPMError as e:
+            if e.status == self.ck.ENOMEM:
+                raise MemoryError(str(e)) from e
+            raise
 
     def release(self, sid: int):
         self.ck.ckmpm_release(self.ctx, sid)
@@ -168,7 +173,11 @@ class Server:
             need = scene_resources(req.scene.n, req.scene.res)
             if not self.budget.fits(self.used, need):
                 break  # FIFO: later requests wait behind the head
-            sid = self.engine.admit(req.scene)
+            try:
+                sid = self.engine.admit(req.scene)
+            except MemoryError:
+                self._blocked = True  # released scenes' particles leave the pool at the next step
+                break
             for k, v in need.items():
                 self.used[k] = self.used.get(k, 0) + v
             self.resident[sid] = {"req": req, "left": req.steps, "need": need, "admitted": self.step_count,
@@ -189,7 +198,11 @@ class Server:
         """Admit, run one global step if anything is resident, retire.  Returns
         False once nothing is waiting or resident."""
         now = self.clock() - self.t0
+        self._blocked = False
         self._admit_ready(now)
+        if self._blocked and not self.resident:
+            self.engine.step()  # nothing resident: this step only compacts the pool
+            self._admit_ready(now)
         if self.resident:
             ms = self.engine.step()
             self.step_count += 1

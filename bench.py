@@ -310,11 +310,15 @@ def run_gpu(args):
     ctxq, keepq = _make_ctx(ck, scene, ck.KERNEL_QUADRATIC, stream_ptr)
     ck.ckmpm_step(ctxq, max(1, args.warmup))
     ck.ckmpm_sync(ctxq)
+    ck.ckmpm_set_timing(ctxq, True)
+    ck.ckmpm_reset_timing(ctxq)
     msq = _time_steps(ck, ctxq, qsteps, stream_ptr)
     ck.ckmpm_sync(ctxq)
+    stq = ck.ckmpm_get_stats(ctxq)
     ck.ckmpm_destroy(ctxq)
     quad = {"value": n * qsteps / (msq / 1e3), "ms_per_step": msq / qsteps, "steps": qsteps,
-            "ck_speedup": (msq / qsteps) / (ms / args.steps)}
+            "ck_speedup": (msq / qsteps) / (ms / args.steps),
+            "per_kernel_ms": {k: stq.ms_kernel[i] for k, i in KERNEL_SLOT.items()}}
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e_steps = max(2, min(args.steps, 10))

@@ -11,6 +11,7 @@ namespace ck {
 struct LaunchCfg {
   cudaStream_t stream;
   int persistent_ctas;  // CTAs of the persistent P2G / update / G2P launches
+  int g2p_minb = 4;     // resident G2P CTAs per SM the register budget targets
 };
 
 enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3 };

@@ -141,11 +141,19 @@ __device__ __forceinline__ void svd3(const T* F, T* U, T* sig, T* V) {
       CK_M(S, i, j) = CK_M(F, 0, i) * CK_M(F, 0, j) + CK_M(F, 1, i) * CK_M(F, 1, j) + CK_M(F, 2, i) * CK_M(F, 2, j);
 #pragma unroll
   for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? T(1) : T(0);
+  // cyclic sweeps until every off-diagonal is below half an ulp of its
+  // diagonal pair (Jacobi converges quadratically; F near a rotation times a
+  // small stretch needs about two sweeps), at most Num<T>::sweeps
 #pragma unroll 1
   for (int sw = 0; sw < Num<T>::sweeps; ++sw) {
     jacobi_rotate(S, V, 0, 1, 2);
     jacobi_rotate(S, V, 0, 2, 1);
     jacobi_rotate(S, V, 1, 2, 0);
+    const T e = Num<T>::eps;
+    if (Num<T>::abs_(CK_M(S, 0, 1)) <= e * (Num<T>::abs_(CK_M(S, 0, 0)) + Num<T>::abs_(CK_M(S, 1, 1))) &&
+        Num<T>::abs_(CK_M(S, 0, 2)) <= e * (Num<T>::abs_(CK_M(S, 0, 0)) + Num<T>::abs_(CK_M(S, 2, 2))) &&
+        Num<T>::abs_(CK_M(S, 1, 2)) <= e * (Num<T>::abs_(CK_M(S, 1, 1)) + Num<T>::abs_(CK_M(S, 2, 2))))
+      break;
   }
   T e[3] = {CK_M(S, 0, 0), CK_M(S, 1, 1), CK_M(S, 2, 2)};
   if (e[0] < e[1]) swap_cols_neg(V, e, 0, 1);

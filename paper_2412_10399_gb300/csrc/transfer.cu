@@ -22,6 +22,25 @@ namespace ck {
 
 constexpr float kInv2Pi = 0.15915494309189535f;
 
+// sin(2 pi f) for f in [0, 1): reduce to t = f - rint(f) in [-1/2, 1/2], fold
+// |t| > 1/4 with sin(2 pi t) = sin(2 pi (sign(t)/2 - t)) (both steps exact in
+// float), then the Taylor series of sin x at x = 2 pi t, |x| <= pi/2, through
+// x^11: coefficients (-1)^k (2 pi)^(2k+1) / (2k+1)!, truncation error below
+// (pi/2)^13 / 13! = 1.5e-8, about 1.6e-7 after float rounding.
+__device__ __forceinline__ float sin_2pi(float f) {
+  float t = f - rintf(f);
+  const float h = copysignf(0.5f, t) - t;
+  t = fabsf(t) > 0.25f ? h : t;
+  const float t2 = t * t;
+  float p = -15.094642576822984f;
+  p = fmaf(p, t2, 42.058693944897634f);
+  p = fmaf(p, t2, -76.70585975306136f);
+  p = fmaf(p, t2, 81.60524927607504f);
+  p = fmaf(p, t2, -41.341702240399755f);
+  p = fmaf(p, t2, 6.283185307179586f);
+  return t * p;
+}
+
 template <int KIND>
 struct Geo;
 template <>
@@ -108,7 +127,7 @@ struct Sten<0> {
       r[0][a] = c.bm - o[a];
       r[1][a] = c.bp - o[a];
       ok = ok && (r[0][a] >= 0) && (r[0][a] <= 3) && (r[1][a] >= 0) && (r[1][a] <= 4);
-      float sg = sinpif(2.0f * c.fp) * kInv2Pi;
+      float sg = sin_2pi(c.fp) * kInv2Pi;
       w[1][a][0] = 1.0f - c.fp + sg;
       w[1][a][1] = c.fp - sg;
       d[1][a][0] = -c.fp;
@@ -122,9 +141,9 @@ struct Sten<0> {
       lam[a] = 0.5f * (m2p + m2m) - sg * sg;
       s[a] = sg;
     }
-    float li[3] = {1.0f / lam[0], 1.0f / lam[1], 1.0f / lam[2]};
+    float li[3] = {__frcp_rn(lam[0]), __frcp_rn(lam[1]), __frcp_rn(lam[2])};
     float y[3] = {li[0] * s[0], li[1] * s[1], li[2] * s[2]};
-    float den = 1.0f / (1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
+    float den = __frcp_rn(1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -219,21 +238,87 @@ __device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, in
 // ------------------------------------------------------------------------ P2G
 
 // Shared-memory accumulation is in 32-bit fixed point: integer shared
-// atomics run about 4x faster than float ones on this part, and integer sums
-// do not depend on the order of the atomics.  A first pass over the block's
-// particles bounds every contribution (|w| <= 1, |x_i - x_p| <= 2 cells,
-// |D^-1| <= 12.5 cells^-2 for both stencils; the smallest eigenvalue of the
-// CK D is 0.0826 cells^2), so with cnt particles no node sum can exceed
-// cnt * bound; the scale maps that to 2^30 (no overflow).  Mass uses one
-// integer; each momentum component is split into a high part (the rounded
-// scaled value) and a low part (the rounding remainder times 2^16), so the
-// sum keeps float precision however loose the bound is.
-constexpr float kDinvBound = 12.5f;
+// atomics run about 4x faster than float ones on this part (measured), and
+// integer sums do not depend on the order of the atomics.  A first pass over
+// the block's particles bounds every contribution each can make (p2g_bound:
+// |w| <= 1, offsets at most dmax cells, rows of D^-1 summing to at most 14.5
+// cells^-2), so with cnt particles no node sum can exceed cnt times the
+// block's largest bound, and the scale maps that to 2^30 (no overflow).
+// Rounding costs at most half a unit per contribution, cnt * bound * 2^-31.
+
+// Particles of a block with at most kP2GStage particles are staged in shared
+// memory by the bound pass (coalesced loads in binned order) and read back by
+// the scatter pass, which takes them C apart per lane; C is odd, so the 32
+// lanes of a warp read 32 distinct banks of the structure-of-arrays copy.
+constexpr int kP2GStage = 544;  // 17 * 32
+
+struct P2GPart {
+  float4 X, a, b, c;
+};
+
+// Largest row abs-sum of D^-1 over all particle positions, in cells^-2: 14.04
+// for the CK dual grid (evaluated over a 121^3 grid of fractions; 14.5 keeps
+// a margin) and 4 for the quadratic B-spline (D^-1 = 4 I).
+template <int KIND>
+struct DinvRowBound;
+template <>
+struct DinvRowBound<0> {
+  static constexpr float value = 14.5f;
+  static constexpr float dmax = 1.0f;  // |x_i - x_p| per axis, cells
+};
+template <>
+struct DinvRowBound<1> {
+  static constexpr float value = 4.0f;
+  static constexpr float dmax = 1.5f;
+};
+
+// Bound of |w (m v + A^ d)|_inf for every node a particle touches (|w| <= 1):
+// m |v|_inf + dmax * max_row sum_k |M_rk| * max_row sum_j |D^-1| / dx.
+template <int KIND>
+__device__ __forceinline__ float p2g_bound(const SceneDev& s, float mass, const P2GPart& q) {
+  const float r0 = fabsf(q.a.w) + fabsf(q.b.x) + fabsf(q.b.y);
+  const float r1 = fabsf(q.b.z) + fabsf(q.b.w) + fabsf(q.c.x);
+  const float r2 = fabsf(q.c.y) + fabsf(q.c.z) + fabsf(q.c.w);
+  const float rm = fmaxf(r0, fmaxf(r1, r2));
+  return mass * fmaxf(fabsf(q.a.x), fmaxf(fabsf(q.a.y), fabsf(q.a.z))) +
+         DinvRowBound<KIND>::dmax * DinvRowBound<KIND>::value * rm * s.inv_dx;
+}
+
+template <int KIND>
+__device__ __forceinline__ void p2g_scatter(const SceneDev& s, const MatDev* mats, uint32_t* err, const P2GPart& q,
+                                            int ox, int oy, int oz, float Sm, float Sp, int (*sm)[Geo<KIND>::NS]) {
+  Sten<KIND> st;
+  if (!st.set(q.X.x * s.inv_dx, q.X.y * s.inv_dx, q.X.z * s.inv_dx, ox, oy, oz)) {
+    flag_error(err, CK_ERR_INTERNAL);
+    return;
+  }
+  float Di[9];
+  dinv_of<KIND>(st, Di);
+  const float M[9] = {q.a.w, q.b.x, q.b.y, q.b.z, q.b.w, q.c.x, q.c.y, q.c.z, q.c.w};
+  // A^ = M D^-1 / dx so that A (x_i - x_p) = A^ (offset in cells), pre-scaled
+  float A[9];
+  const float ks = s.inv_dx * Sp;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      A[r * 3 + k] = (M[r * 3 + 0] * Di[0 * 3 + k] + M[r * 3 + 1] * Di[1 * 3 + k] + M[r * 3 + 2] * Di[2 * 3 + k]) * ks;
+  const float mass = mats[__float_as_uint(q.X.w)].mass;
+  const float ms = mass * Sm;
+  const float px = mass * q.a.x * Sp, py = mass * q.a.y * Sp, pz = mass * q.a.z * Sp;
+  for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
+    atomicAdd(&sm[0][j], __float2int_rn(w * ms));
+    atomicAdd(&sm[1][j], __float2int_rn(w * (px + A[0] * dx + A[1] * dy + A[2] * dz)));
+    atomicAdd(&sm[2][j], __float2int_rn(w * (py + A[3] * dx + A[4] * dy + A[5] * dz)));
+    atomicAdd(&sm[3][j], __float2int_rn(w * (pz + A[6] * dx + A[7] * dy + A[8] * dz)));
+  });
+}
 
 template <int KIND>
 __global__ void __launch_bounds__(128) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  __shared__ int sm[7][NS];
+  __shared__ int sm[4][NS];
+  __shared__ float sp[16][kP2GStage];
   __shared__ uint32_t bslot[8];
   __shared__ float sred[2][4];
   const uint32_t npb = *v.n_pb;
@@ -248,82 +333,55 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
     load_block_slots(v, s, ox, oy, oz, bslot);
     for (int j = threadIdx.x; j < NS; j += blockDim.x) {
 #pragma unroll
-      for (int c = 0; c < 7; ++c) sm[c][j] = 0;
+      for (int c = 0; c < 4; ++c) sm[c][j] = 0;
     }
-    // pass 1: bounds of |m v| and of the affine term over the block
-    float bv = 0.f, bm = 0.f;
+    const uint32_t C = ((cnt + 31u) >> 5) | 1u;
+    const bool staged = (C << 5) <= (uint32_t)kP2GStage;
+    // pass 1: the largest contribution any particle of the block can make
+    float bmass = 0.f, bmom = 0.f;
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
       const uint32_t p = v.perm[start + i];
-      const float4 a = v.cur.VM0[p];
-      const float4 b = v.cur.VM1[p];
-      const float4 c = v.cur.VM2[p];
-      bv = fmaxf(bv, fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))));
-      float r0 = fabsf(a.w) + fabsf(b.x) + fabsf(b.y);
-      float r1 = fabsf(b.z) + fabsf(b.w) + fabsf(c.x);
-      float r2 = fabsf(c.y) + fabsf(c.z) + fabsf(c.w);
-      bm = fmaxf(bm, fmaxf(r0, fmaxf(r1, r2)));
+      P2GPart q{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
+      if (staged) {
+        const float* f = reinterpret_cast<const float*>(&q);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sp[k][i] = f[k];
+      }
+      const float mass = v.mats[__float_as_uint(q.X.w)].mass;
+      bmom = fmaxf(bmom, p2g_bound<KIND>(s, mass, q));
+      bmass = fmaxf(bmass, mass);
     }
     for (int o = 16; o > 0; o >>= 1) {
-      bv = fmaxf(bv, __shfl_xor_sync(0xffffffffu, bv, o));
-      bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      bmass = fmaxf(bmass, __shfl_xor_sync(0xffffffffu, bmass, o));
+      bmom = fmaxf(bmom, __shfl_xor_sync(0xffffffffu, bmom, o));
     }
     if (lane == 0) {
-      sred[0][warp] = bv;
-      sred[1][warp] = bm;
+      sred[0][warp] = bmass;
+      sred[1][warp] = bmom;
     }
     __syncthreads();
-    bv = fmaxf(fmaxf(sred[0][0], sred[0][1]), fmaxf(sred[0][2], sred[0][3]));
-    bm = fmaxf(fmaxf(sred[1][0], sred[1][1]), fmaxf(sred[1][2], sred[1][3]));
+    bmass = fmaxf(fmaxf(sred[0][0], sred[0][1]), fmaxf(sred[0][2], sred[0][3]));
+    bmom = fmaxf(fmaxf(sred[1][0], sred[1][1]), fmaxf(sred[1][2], sred[1][3]));
     const float fcnt = (float)cnt;
-    const float bound_p = s.mmax * bv + 2.0f * 3.0f * kDinvBound * bm * s.inv_dx;
-    const float Sm = 1073741824.0f / (fcnt * s.mmax);
-    const float Sp = bound_p > 0.f ? 1073741824.0f / (fcnt * bound_p) : 1.0f;
-    // pass 2: lanes of a warp take particles C = ceil(cnt/32) apart in the
-    // block's order; particles of one cell sit next to each other (sampling
-    // order, kept by the binning), so neighbouring lanes come from different
-    // cells and their atomics hit different nodes instead of serialising.
-    const uint32_t C = (cnt + 31u) >> 5;
-    for (uint32_t q = threadIdx.x; q < (C << 5); q += blockDim.x) {
-      const uint32_t i = (q & 31u) * C + (q >> 5);
+    const float Sm = bmass > 0.f ? 1073741824.0f / (fcnt * bmass) : 1.0f;
+    const float Sp = bmom > 0.f ? 1073741824.0f / (fcnt * bmom) : 1.0f;
+    // pass 2: lanes of a warp take particles C apart in the block's order;
+    // particles of one cell sit next to each other (sampling order, kept by
+    // the binning), so neighbouring lanes come from different cells and their
+    // atomics hit different nodes instead of serialising on one address.
+    for (uint32_t qq = threadIdx.x; qq < (C << 5); qq += blockDim.x) {
+      const uint32_t i = (qq & 31u) * C + (qq >> 5);
       if (i >= cnt) continue;
-      const uint32_t p = v.perm[start + i];
-      const float4 X = v.cur.X[p];
-      const float4 a = v.cur.VM0[p];
-      const float4 b = v.cur.VM1[p];
-      const float4 c = v.cur.VM2[p];
-      const MatDev mt = v.mats[__float_as_uint(X.w)];
-      Sten<KIND> st;
-      if (!st.set(X.x * s.inv_dx, X.y * s.inv_dx, X.z * s.inv_dx, ox, oy, oz)) {
-        flag_error(v.err, CK_ERR_INTERNAL);
-        continue;
+      P2GPart q;
+      if (staged) {
+        float* f = reinterpret_cast<float*>(&q);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) f[k] = sp[k][i];
+      } else {
+        const uint32_t p = v.perm[start + i];
+        q = P2GPart{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
       }
-      float Di[9];
-      dinv_of<KIND>(st, Di);
-      const float M[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-      // A^ = M D^-1 / dx so that A (x_i - x_p) = A^ (offset in cells), pre-scaled
-      float A[9];
-      const float ks = s.inv_dx * Sp;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int qq = 0; qq < 3; ++qq)
-          A[r * 3 + qq] = (M[r * 3 + 0] * Di[0 * 3 + qq] + M[r * 3 + 1] * Di[1 * 3 + qq] + M[r * 3 + 2] * Di[2 * 3 + qq]) * ks;
-      const float m = mt.mass;
-      const float ms = m * Sm;
-      const float px = m * a.x * Sp, py = m * a.y * Sp, pz = m * a.z * Sp;
-      for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
-        atomicAdd(&sm[0][j], __float2int_rn(w * ms));
-        const float vx = w * (px + A[0] * dx + A[1] * dy + A[2] * dz);
-        const float vy = w * (py + A[3] * dx + A[4] * dy + A[5] * dz);
-        const float vz = w * (pz + A[6] * dx + A[7] * dy + A[8] * dz);
-        const float hx = rintf(vx), hy = rintf(vy), hz = rintf(vz);
-        atomicAdd(&sm[1][j], (int)hx);
-        atomicAdd(&sm[2][j], __float2int_rn((vx - hx) * 65536.0f));
-        atomicAdd(&sm[3][j], (int)hy);
-        atomicAdd(&sm[4][j], __float2int_rn((vy - hy) * 65536.0f));
-        atomicAdd(&sm[5][j], (int)hz);
-        atomicAdd(&sm[6][j], __float2int_rn((vz - hz) * 65536.0f));
-      });
+      p2g_scatter<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
     }
     __syncthreads();
     const float iSm = 1.0f / Sm, iSp = 1.0f / Sp;
@@ -333,13 +391,9 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
         int g, lx, ly, lz;
         staged_coords<KIND>(j, g, lx, ly, lz);
         long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
-        if (gi >= 0) {
-          const float l16 = 1.0f / 65536.0f;
-          float4 o = make_float4((float)mi * iSm, ((float)sm[1][j] + (float)sm[2][j] * l16) * iSp,
-                                 ((float)sm[3][j] + (float)sm[4][j] * l16) * iSp,
-                                 ((float)sm[5][j] + (float)sm[6][j] * l16) * iSp);
-          atomicAdd(&v.Gacc[gi], o);
-        }
+        if (gi >= 0)
+          atomicAdd(&v.Gacc[gi], make_float4((float)mi * iSm, (float)sm[1][j] * iSp, (float)sm[2][j] * iSp,
+                                             (float)sm[3][j] * iSp));
       }
     }
     __syncthreads();
@@ -386,10 +440,10 @@ __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
 
 __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(a, fminf(b, c)); }
 
-template <int KIND>
-__global__ void __launch_bounds__(128, 4) k_g2p(StepView v) {
+template <int KIND, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  __shared__ float sv[3][NS];
+  __shared__ float4 sv[NS];  // staged v~ (w unused): one 16-byte shared load per node
   __shared__ uint32_t bslot[8];
   const uint32_t npb = *v.n_pb;
   for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
@@ -405,10 +459,7 @@ __global__ void __launch_bounds__(128, 4) k_g2p(StepView v) {
       int g, lx, ly, lz;
       staged_coords<KIND>(j, g, lx, ly, lz);
       long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
-      float4 gv = gi >= 0 ? v.Gvel[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-      sv[0][j] = gv.x;
-      sv[1][j] = gv.y;
-      sv[2][j] = gv.z;
+      sv[j] = gi >= 0 ? v.Gvel[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -438,7 +489,8 @@ __global__ void __launch_bounds__(128, 4) k_g2p(StepView v) {
 #pragma unroll
       for (int q = 0; q < 9; ++q) Bh[q] = 0.f;
       for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
-        float gx = sv[0][j] * w, gy = sv[1][j] * w, gz = sv[2][j] * w;
+        const float4 g4 = sv[j];
+        float gx = g4.x * w, gy = g4.y * w, gz = g4.z * w;
         vx += gx;
         vy += gy;
         vz += gz;
@@ -803,7 +855,16 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
     case LK_P2G: k_p2g<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
     case LK_UPDATE: k_grid_update<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
-    case LK_G2P: k_g2p<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+    case LK_G2P:
+      // register budget of G2P: 4 CTAs/SM (128 registers) by default; the
+      // CKMPM_G2P_MINB environment variable selects 5 or 6 (102 / 85)
+      if (lc.g2p_minb >= 6)
+        k_g2p<KIND, 6><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
+      else if (lc.g2p_minb == 5)
+        k_g2p<KIND, 5><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
+      else
+        k_g2p<KIND, 4><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
+      break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
   }
 }

@@ -175,6 +175,28 @@ __device__ __forceinline__ void svd3(const T* F, T* U, T* sig, T* V) {
   sig[2] = CK_M(Bm, 2, 2);
 }
 
+// Symmetric eigen-decomposition S = Q diag(e) Q^T by the same cyclic Jacobi
+// sweeps (no sorting); S is overwritten.
+template <typename T>
+__device__ __forceinline__ void sym_eig3(T* S, T* Q, T* e) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? T(1) : T(0);
+#pragma unroll 1
+  for (int sw = 0; sw < Num<T>::sweeps; ++sw) {
+    jacobi_rotate(S, Q, 0, 1, 2);
+    jacobi_rotate(S, Q, 0, 2, 1);
+    jacobi_rotate(S, Q, 1, 2, 0);
+    const T ep = Num<T>::eps;
+    if (Num<T>::abs_(CK_M(S, 0, 1)) <= ep * (Num<T>::abs_(CK_M(S, 0, 0)) + Num<T>::abs_(CK_M(S, 1, 1))) &&
+        Num<T>::abs_(CK_M(S, 0, 2)) <= ep * (Num<T>::abs_(CK_M(S, 0, 0)) + Num<T>::abs_(CK_M(S, 2, 2))) &&
+        Num<T>::abs_(CK_M(S, 1, 2)) <= ep * (Num<T>::abs_(CK_M(S, 1, 1)) + Num<T>::abs_(CK_M(S, 2, 2))))
+      break;
+  }
+  e[0] = CK_M(S, 0, 0);
+  e[1] = CK_M(S, 1, 1);
+  e[2] = CK_M(S, 2, 2);
+}
+
 // ---------------------------------------------------------------- materials
 
 constexpr float kSigmaFloor = 1e-6f;
@@ -266,6 +288,69 @@ __device__ __forceinline__ void constitutive(int model, T* F, T mu, T lam, T alp
   sig_out[0] = sig[0];
   sig_out[1] = sig[1];
   sig_out[2] = sig[2];
+}
+
+// Constitutive update from the left stretch: b = F F^T = U diag(sigma^2) U^T
+// gives U and sigma without V (F = U Sigma V^T, det F > 0).  Drucker-Prager:
+// F <- U diag(sigma_new / sigma) U^T F (= U Sigma_new V^T) and the Hencky
+// stress U diag(2 mu eps + lam tr eps) U^T; fixed-corotated: R = U diag(1 /
+// sigma) U^T F (= U V^T) and 2 mu (F - R) F^T + lam J (J - 1) I.  Used in
+// float32 for well-conditioned F with det F > 0; sig_out gets sigma.
+template <typename T>
+__device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, T alpha, T* tau, T* sig_out,
+                                                  const T* U, const T* sig) {
+  if (model == 1) {
+    T sn[3] = {sig[0], sig[1], sig[2]};
+    if (dp_project<T>(sn, mu, lam, alpha)) {
+      T k[3] = {sn[0] / sig[0], sn[1] / sig[1], sn[2] / sig[2]};
+      T W[9], Fn[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          CK_M(W, i, j) = CK_M(U, i, 0) * k[0] * CK_M(U, j, 0) + CK_M(U, i, 1) * k[1] * CK_M(U, j, 1) +
+                          CK_M(U, i, 2) * k[2] * CK_M(U, j, 2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          CK_M(Fn, i, j) = CK_M(W, i, 0) * CK_M(F, 0, j) + CK_M(W, i, 1) * CK_M(F, 1, j) + CK_M(W, i, 2) * CK_M(F, 2, j);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) F[q] = Fn[q];
+    }
+    hencky_tau<T>(U, sn, mu, lam, tau);
+    sig_out[0] = sn[0];
+    sig_out[1] = sn[1];
+    sig_out[2] = sn[2];
+  } else {
+    T k[3] = {T(1) / sig[0], T(1) / sig[1], T(1) / sig[2]};
+    T W[9], R[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        CK_M(W, i, j) = CK_M(U, i, 0) * k[0] * CK_M(U, j, 0) + CK_M(U, i, 1) * k[1] * CK_M(U, j, 1) +
+                        CK_M(U, i, 2) * k[2] * CK_M(U, j, 2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        CK_M(R, i, j) = CK_M(W, i, 0) * CK_M(F, 0, j) + CK_M(W, i, 1) * CK_M(F, 1, j) + CK_M(W, i, 2) * CK_M(F, 2, j);
+    const T J = sig[0] * sig[1] * sig[2];
+    T D[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) D[i] = F[i] - R[i];
+    const T vol = lam * J * (J - T(1));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        CK_M(tau, i, j) = T(2) * mu * (CK_M(D, i, 0) * CK_M(F, j, 0) + CK_M(D, i, 1) * CK_M(F, j, 1) + CK_M(D, i, 2) * CK_M(F, j, 2)) +
+                          (i == j ? vol : T(0));
+    sig_out[0] = sig[0];
+    sig_out[1] = sig[1];
+    sig_out[2] = sig[2];
+  }
 }
 
 // Kirchhoff stress of a given F without plasticity (used by readback/upload).

@@ -22,6 +22,20 @@ namespace ck {
 
 constexpr float kInv2Pi = 0.15915494309189535f;
 
+// Asynchronous global -> shared copies (cp.async, cached in L1 and L2): a CTA
+// issues the gathers of a whole particle block before it waits for any.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // sin(2 pi f) for f in [0, 1): reduce to t = f - rint(f) in [-1/2, 1/2], fold
 // |t| > 1/4 with sin(2 pi t) = sin(2 pi (sign(t)/2 - t)) (both steps exact in
 // float), then the Taylor series of sin x at x = 2 pi t, |x| <= pi/2, through
@@ -246,10 +260,11 @@ __device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, in
 // block's largest bound, and the scale maps that to 2^30 (no overflow).
 // Rounding costs at most half a unit per contribution, cnt * bound * 2^-31.
 
-// Particles of a block with at most kP2GStage particles are staged in shared
-// memory by the bound pass (coalesced loads in binned order) and read back by
-// the scatter pass, which takes them C apart per lane; C is odd, so the 32
-// lanes of a warp read 32 distinct banks of the structure-of-arrays copy.
+// Particles of a block with at most kP2GStage particles are copied into
+// shared memory up front (cp.async gathers through the binned order, all in
+// flight together) and read back by both passes; the scatter pass takes them
+// C apart per lane with C odd, so each quarter-warp's 16-byte reads fall on
+// distinct bank groups.
 constexpr int kP2GStage = 544;  // 17 * 32
 
 struct P2GPart {
@@ -318,7 +333,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   __shared__ int sm[4][NS];
-  __shared__ float sp[16][kP2GStage];
+  __shared__ float4 sX[kP2GStage], sA[kP2GStage], sB[kP2GStage], sC[kP2GStage];
   __shared__ uint32_t bslot[8];
   __shared__ float sred[2][4];
   const uint32_t npb = *v.n_pb;
@@ -337,15 +352,27 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
     }
     const uint32_t C = ((cnt + 31u) >> 5) | 1u;
     const bool staged = (C << 5) <= (uint32_t)kP2GStage;
+    if (staged) {
+#pragma unroll 4
+      for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint32_t p = v.perm[start + i];
+        cp_async16(&sX[i], &v.cur.X[p]);
+        cp_async16(&sA[i], &v.cur.VM0[p]);
+        cp_async16(&sB[i], &v.cur.VM1[p]);
+        cp_async16(&sC[i], &v.cur.VM2[p]);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
     // pass 1: the largest contribution any particle of the block can make
     float bmass = 0.f, bmom = 0.f;
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const uint32_t p = v.perm[start + i];
-      P2GPart q{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
+      P2GPart q;
       if (staged) {
-        const float* f = reinterpret_cast<const float*>(&q);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sp[k][i] = f[k];
+        q = P2GPart{sX[i], sA[i], sB[i], sC[i]};
+      } else {
+        const uint32_t p = v.perm[start + i];
+        q = P2GPart{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
       }
       const float mass = v.mats[__float_as_uint(q.X.w)].mass;
       bmom = fmaxf(bmom, p2g_bound<KIND>(s, mass, q));
@@ -374,9 +401,7 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
       if (i >= cnt) continue;
       P2GPart q;
       if (staged) {
-        float* f = reinterpret_cast<float*>(&q);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) f[k] = sp[k][i];
+        q = P2GPart{sX[i], sA[i], sB[i], sC[i]};
       } else {
         const uint32_t p = v.perm[start + i];
         q = P2GPart{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
@@ -440,10 +465,16 @@ __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
 
 __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(a, fminf(b, c)); }
 
+constexpr int kG2PStage = 512;  // particles staged per chunk
+
 template <int KIND, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
+  constexpr int CAP = kG2PStage;
   __shared__ float4 sv[NS];  // staged v~ (w unused): one 16-byte shared load per node
+  __shared__ float4 sX[CAP], sF0[CAP], sF1[CAP];
+  __shared__ float sF2[CAP], sE[CAP];
+  __shared__ uint32_t sID[CAP];
   __shared__ uint32_t bslot[8];
   const uint32_t npb = *v.n_pb;
   for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
@@ -455,27 +486,43 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
     __syncthreads();
-    for (int j = threadIdx.x; j < NS; j += blockDim.x) {
-      int g, lx, ly, lz;
-      staged_coords<KIND>(j, g, lx, ly, lz);
-      long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
-      sv[j] = gi >= 0 ? v.Gvel[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
+    const uint32_t m = min(cnt - c0, (uint32_t)CAP);
+    // the chunk's particle state: cp.async gathers through the binned order,
+    // all in flight while the grid velocities are staged
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const uint32_t p = v.perm[start + c0 + i];
+      cp_async16(&sX[i], &v.cur.X[p]);
+      cp_async16(&sF0[i], &v.cur.F0[p]);
+      cp_async16(&sF1[i], &v.cur.F1[p]);
+      cp_async4(&sF2[i], &v.cur.F2[p]);
+      cp_async4(&sID[i], &v.cur.ID[p]);
+      if (v.cur.E) cp_async4(&sE[i], &v.cur.E[p]);
     }
+    if (c0 == 0) {
+      for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+        int g, lx, ly, lz;
+        staged_coords<KIND>(j, g, lx, ly, lz);
+        long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
+        sv[j] = gi >= 0 ? v.Gvel[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    cp_async_wait_all();
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const uint32_t t = start + i;
-      const uint32_t p = v.perm[t];
-      const float4 X = v.cur.X[p];
-      const float4 f0 = v.cur.F0[p];
-      const float4 f1 = v.cur.F1[p];
-      const float f2 = v.cur.F2[p];
-      const uint32_t id = v.cur.ID[p];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const uint32_t t = start + c0 + i;
+      const float4 X = sX[i];
+      const float4 f0 = sF0[i];
+      const float4 f1 = sF1[i];
+      const float f2 = sF2[i];
+      const uint32_t id = sID[i];
       const uint32_t mi = __float_as_uint(X.w);
       const MatDev mt = v.mats[mi];
       float mu = mt.mu, lam = mt.lam;
       float Ep = 0.f;
       if (v.cur.E) {
-        Ep = v.cur.E[p];
+        Ep = sE[i];
         mu = Ep / (2.0f * (1.0f + mt.nu));
         lam = Ep * mt.nu / ((1.0f + mt.nu) * (1.0f - 2.0f * mt.nu));
       }
@@ -525,14 +572,29 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
       // constitutive update; float64 redo for degenerate F (precision extension)
       float tau[9];
       {
-        float U[9], V[9], sg[3];
-        svd3<float>(F, U, sg, V);
-        float a0 = fabsf(sg[0]), a1 = fabsf(sg[1]), a2 = fabsf(sg[2]);
-        float smax = fmaxf(a0, fmaxf(a1, a2));
-        float smin = min3(a0, a1, a2);
-        float J = sg[0] * sg[1] * sg[2];
-        float gap = min3(fabsf(a0 - a1), fabsf(a0 - a2), fabsf(a1 - a2));
-        bool use64 = (fabsf(J) < s.j_tol) || (smin < s.cond_tol * smax) || (gap < s.gap_tol * smax);
+        // float32: left stretch b = F F^T = U diag(sigma^2) U^T
+        float bq[9], U[9], e[3], sg[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int q = r; q < 3; ++q) {
+            const float d = F[r * 3] * F[q * 3] + F[r * 3 + 1] * F[q * 3 + 1] + F[r * 3 + 2] * F[q * 3 + 2];
+            bq[r * 3 + q] = d;
+            bq[q * 3 + r] = d;
+          }
+        sym_eig3<float>(bq, U, e);
+        sg[0] = sqrtf(fmaxf(e[0], 0.f));
+        sg[1] = sqrtf(fmaxf(e[1], 0.f));
+        sg[2] = sqrtf(fmaxf(e[2], 0.f));
+        const float J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                        F[2] * (F[3] * F[7] - F[4] * F[6]);
+        const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
+        const float smin = min3(sg[0], sg[1], sg[2]);
+        const float gap = min3(fabsf(sg[0] - sg[1]), fabsf(sg[0] - sg[2]), fabsf(sg[1] - sg[2]));
+        // float64 (full rotation-variant SVD) where F is degenerate, inverted or
+        // the criteria of the scene ask for it
+        const bool use64 = !(J > 0.f) || (fabsf(J) < s.j_tol) || (smin < s.cond_tol * smax) ||
+                           (gap < s.gap_tol * smax);
         if (use64) {
           double Fd[9], taud[9], sgd[3];
 #pragma unroll
@@ -545,12 +607,8 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
           }
           atomicAdd(v.fp64_count, 1ull);
         } else {
-          if (mt.model == 1) {
-            if (dp_project<float>(sg, mu, lam, mt.alpha)) usvt<float>(U, sg, V, F);
-            hencky_tau<float>(U, sg, mu, lam, tau);
-          } else {
-            fc_tau<float>(F, U, sg, V, mu, lam, tau);
-          }
+          float so[3];
+          constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, so, U, sg);
         }
       }
       // M' = m B' - dt V0 tau, B' = dx Bh
@@ -591,7 +649,8 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
       v.key_nxt[t] = nk;
       warp_aggregated_inc(v.cnt_nxt, nk);
     }
-    __syncthreads();
+    __syncthreads();  // the next chunk (or block) overwrites the staged copies
+    }
   }
 }
 

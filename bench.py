@@ -91,6 +91,21 @@ def _traffic(kernel):
         return None
 
 
+def aggregate_ranks(ms_local: float, particles_local: int, steps: int, dist=None, device="cpu"):
+    """Whole-job throughput across ranks (weak scaling, one replica per rank):
+    the slowest rank's time over the particles all ranks advanced.  Returns
+    (value particle-steps/s, max ms).  With dist=None this is the one-rank case."""
+    import torch
+    if dist is None:
+        return particles_local * steps / (ms_local / 1e3), ms_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([particles_local], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return float(n.item()) * steps / (ms / 1e3), ms
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -282,10 +297,8 @@ def run_gpu(args):
     ck.ckmpm_sync(ctx)
     st = ck.ckmpm_get_stats(ctx)
     ck.ckmpm_set_timing(ctx, False)
+    value, ms = aggregate_ranks(ms, n, args.steps, dist, device="cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     per_kernel = {k: st.ms_kernel[i] for k, i in KERNEL_SLOT.items()}
     launches = int(st.launches_per_step) * args.steps
@@ -293,7 +306,6 @@ def run_gpu(args):
     n_pb, n_gb = int(st.n_particle_blocks), int(st.n_grid_blocks)
     ck.ckmpm_destroy(ctx)
 
-    value = world * n * args.steps / (ms / 1e3)
     dominant = max(("p2g", "g2p"), key=lambda k: per_kernel[k])
     peak, peak_src = _peaks()
     achieved = ALGO_BYTES[dominant] * n / (per_kernel[dominant] / 1e3) / 1e9

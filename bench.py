@@ -43,7 +43,7 @@ WORKLOAD = "large_impact: 512^3 virtual grid (dx 1/512), DP sand castle + 4 FC b
 #   G2P: read x 12 + F 36, gather 2 grids x 12 B / 8 = 3, write x 12 + v 12 + M 36 + F 36 -> 147 B
 #   grid update: per node read 16 + write 12 B, 2 grids / 8 -> 7 B
 ALGO_BYTES = {"p2g": 64.0, "g2p": 147.0, "grid_update": 7.0}
-KERNEL_SLOT = {"bin": 0, "scatter": 1, "p2g": 2, "grid_update": 3, "g2p": 4, "grid_list": 5}
+KERNEL_SLOT = {"bin": 0, "scatter": 1, "p2g": 2, "grid_update": 3, "g2p": 4, "grid_list": 5, "g2p_fp64": 6}
 
 
 def _env_rank():

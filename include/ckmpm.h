@@ -138,11 +138,12 @@ typedef struct {
   int64_t n_particle_blocks;  /* non-empty particle blocks in the last step */
   int64_t n_grid_blocks;      /* active grid blocks in the last step */
   int64_t steps;              /* global steps taken */
-  int64_t fp64_particles;     /* particles that took the float64 SVD in the last step */
+  int64_t fp64_particles;     /* particles of the last step's float64 pass */
   double ms_last_step;        /* device time of the last step (timing on) */
   double ms_kernel[8];        /* average device ms per launch per kernel since the
                                  last ckmpm_reset_timing(): 0 bin, 1 scatter,
-                                 2 p2g, 3 grid update, 4 g2p, 5 grid list */
+                                 2 p2g, 3 grid update, 4 g2p, 5 grid list,
+                                 6 float64 pass */
   int64_t launches_kernel[8]; /* launches counted in ms_kernel */
   int64_t launches_per_step;  /* kernel launches issued by one step */
 } ckmpm_stats;

@@ -101,6 +101,7 @@ struct ckmpm_ctx {
   uint32_t* cnt[2]{};
   uint32_t *offset = nullptr, *cursor = nullptr, *perm = nullptr, *pb_key = nullptr, *pb_scene = nullptr;
   uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit)
+  uint32_t* fp64_list = nullptr;  // particles of the float64 pass (capacity cap_n)
   uint32_t *gflag = nullptr, *table = nullptr, *g_list = nullptr, *g_scene = nullptr;
   uint32_t *tile_cnt = nullptr, *tile_ne = nullptr, *scene_tab = nullptr;
   float4 *Gacc = nullptr, *Gvel = nullptr;
@@ -213,6 +214,7 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.n_g = ctx->counters + 1;
   v.err = ctx->counters + 2;
   v.fp64_count = (unsigned long long*)(ctx->counters + 4);
+  v.fp64_list = ctx->fp64_list;
   v.gflag = ctx->gflag;
   v.table = ctx->table;
   v.pool_cap = (uint32_t)ctx->cap_pool;
@@ -402,6 +404,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   int per_sm = 8;
   if (const char* e = getenv("CKMPM_CTAS_PER_SM")) per_sm = std::max(1, atoi(e));
   ctx->lc.persistent_ctas = ctx->sm_count * per_sm;
+  ctx->lc.sm_count = ctx->sm_count;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
@@ -420,7 +423,8 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   const int NG = ctx->kind == 0 ? 2 : 1;
   bool ok = alloc_pool(ctx, ctx->pool[0], ctx->cap_n) && alloc_pool(ctx, ctx->pool[1], ctx->cap_n) &&
             alloc_n(ctx, ctx->key[0], ctx->cap_n) && alloc_n(ctx, ctx->key[1], ctx->cap_n) &&
-            alloc_n(ctx, ctx->perm, ctx->cap_n) && alloc_n(ctx, ctx->cnt[0], ctx->cap_keys) &&
+            alloc_n(ctx, ctx->perm, ctx->cap_n) && alloc_n(ctx, ctx->fp64_list, ctx->cap_n) &&
+            alloc_n(ctx, ctx->cnt[0], ctx->cap_keys) &&
             alloc_n(ctx, ctx->cnt[1], ctx->cap_keys) && alloc_n(ctx, ctx->offset, ctx->cap_keys) &&
             alloc_n(ctx, ctx->cursor, ctx->cap_keys) && alloc_n(ctx, ctx->pb_key, ctx->cap_keys) &&
             alloc_n(ctx, ctx->pb_scene, ctx->cap_keys) && alloc_n(ctx, ctx->counters, 8) &&
@@ -520,6 +524,9 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   }
   tbeg(ctx, ep, 4);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_G2P);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 6);
+  ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_G2P_FP64);
   tend(ctx, ep);
   if (ctx->timing) cudaEventRecord(ctx->step_b, ctx->stream);
   CK_TRY(cudaGetLastError(), "step launch");
@@ -908,7 +915,7 @@ ckmpm_status ckmpm_get_stats(ckmpm_ctx* ctx, ckmpm_stats* out) {
     out->ms_kernel[i] = ctx->ms_cnt[i] ? ctx->ms_sum[i] / ctx->ms_cnt[i] : 0.0;
     out->launches_kernel[i] = ctx->ms_cnt[i];
   }
-  out->launches_per_step = 8;
+  out->launches_per_step = 9;
   return CKMPM_OK;
 }
 

@@ -290,19 +290,42 @@ __device__ __forceinline__ void constitutive(int model, T* F, T mu, T lam, T alp
   sig_out[2] = sig[2];
 }
 
-// Constitutive update from the left stretch: b = F F^T = U diag(sigma^2) U^T
-// gives U and sigma without V (F = U Sigma V^T, det F > 0).  Drucker-Prager:
-// F <- U diag(sigma_new / sigma) U^T F (= U Sigma_new V^T) and the Hencky
-// stress U diag(2 mu eps + lam tr eps) U^T; fixed-corotated: R = U diag(1 /
-// sigma) U^T F (= U V^T) and 2 mu (F - R) F^T + lam J (J - 1) I.  Used in
-// float32 for well-conditioned F with det F > 0; sig_out gets sigma.
+// Constitutive update from the left stretch: b = F F^T = U diag(e) U^T,
+// e = sigma^2, gives U and sigma without V (F = U Sigma V^T, det F > 0).
+// Drucker-Prager works on the log strains eps = ln(e) / 2 directly: the
+// return map gives eps_new, then F <- U diag(exp(eps_new - eps)) U^T F
+// (= U Sigma_new V^T) and the Hencky stress U diag(2 mu eps_new + lam tr
+// eps_new) U^T, with no log of the projected sigma and no division.
+// Fixed-corotated: R = U diag(1 / sigma) U^T F (= U V^T) and 2 mu (F - R) F^T
+// + lam J (J - 1) I.  Used in float32 for well-conditioned F with det F > 0.
 template <typename T>
-__device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, T alpha, T* tau, T* sig_out,
-                                                  const T* U, const T* sig) {
+__device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, T alpha, T* tau, const T* U,
+                                                  const T* e, const T* sig) {
   if (model == 1) {
-    T sn[3] = {sig[0], sig[1], sig[2]};
-    if (dp_project<T>(sn, mu, lam, alpha)) {
-      T k[3] = {sn[0] / sig[0], sn[1] / sig[1], sn[2] / sig[2]};
+    const T fl = T(kSigmaFloor) * T(kSigmaFloor);
+    T ep[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ep[a] = T(0.5) * Num<T>::log_(e[a] > fl ? e[a] : fl);
+    const T tr = ep[0] + ep[1] + ep[2];
+    const T h0 = ep[0] - tr / T(3), h1 = ep[1] - tr / T(3), h2 = ep[2] - tr / T(3);
+    const T nrm = Num<T>::sqrt_(h0 * h0 + h1 * h1 + h2 * h2);
+    T en[3] = {ep[0], ep[1], ep[2]};
+    bool moved = false;
+    if (tr >= T(0) || nrm <= T(0)) {  // tension or purely volumetric: the tip
+      en[0] = en[1] = en[2] = T(0);
+      moved = true;
+    } else {
+      const T dg = nrm + (T(3) * lam + T(2) * mu) / (T(2) * mu) * tr * alpha;
+      if (dg > T(0)) {
+        const T k = dg / nrm;
+        en[0] = ep[0] - k * h0;
+        en[1] = ep[1] - k * h1;
+        en[2] = ep[2] - k * h2;
+        moved = true;
+      }
+    }
+    if (moved) {
+      const T k[3] = {Num<T>::exp_(en[0] - ep[0]), Num<T>::exp_(en[1] - ep[1]), Num<T>::exp_(en[2] - ep[2])};
       T W[9], Fn[9];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -318,10 +341,14 @@ __device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, 
 #pragma unroll
       for (int q = 0; q < 9; ++q) F[q] = Fn[q];
     }
-    hencky_tau<T>(U, sn, mu, lam, tau);
-    sig_out[0] = sn[0];
-    sig_out[1] = sn[1];
-    sig_out[2] = sn[2];
+    const T trn = en[0] + en[1] + en[2];
+    const T d0 = T(2) * mu * en[0] + lam * trn, d1 = T(2) * mu * en[1] + lam * trn, d2 = T(2) * mu * en[2] + lam * trn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        CK_M(tau, i, j) = CK_M(U, i, 0) * d0 * CK_M(U, j, 0) + CK_M(U, i, 1) * d1 * CK_M(U, j, 1) +
+                          CK_M(U, i, 2) * d2 * CK_M(U, j, 2);
   } else {
     T k[3] = {T(1) / sig[0], T(1) / sig[1], T(1) / sig[2]};
     T W[9], R[9];
@@ -347,9 +374,6 @@ __device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, 
       for (int j = 0; j < 3; ++j)
         CK_M(tau, i, j) = T(2) * mu * (CK_M(D, i, 0) * CK_M(F, j, 0) + CK_M(D, i, 1) * CK_M(F, j, 1) + CK_M(D, i, 2) * CK_M(F, j, 2)) +
                           (i == j ? vol : T(0));
-    sig_out[0] = sig[0];
-    sig_out[1] = sig[1];
-    sig_out[2] = sig[2];
   }
 }
 

@@ -569,10 +569,12 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
 #pragma unroll
         for (int q = 0; q < 3; ++q)
           F[r * 3 + q] = G[r * 3 + 0] * Fo[0 * 3 + q] + G[r * 3 + 1] * Fo[1 * 3 + q] + G[r * 3 + 2] * Fo[2 * 3 + q];
-      // constitutive update; float64 redo for degenerate F (precision extension)
+      // constitutive update in float32 from the left stretch; degenerate or
+      // inverted F is deferred to the float64 pass (precision extension):
+      // this kernel stores F' and M = m B' (no stress) and lists the particle
       float tau[9];
       {
-        // float32: left stretch b = F F^T = U diag(sigma^2) U^T
+        // b = F F^T = U diag(sigma^2) U^T
         float bq[9], U[9], e[3], sg[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -591,24 +593,15 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
         const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
         const float smin = min3(sg[0], sg[1], sg[2]);
         const float gap = min3(fabsf(sg[0] - sg[1]), fabsf(sg[0] - sg[2]), fabsf(sg[1] - sg[2]));
-        // float64 (full rotation-variant SVD) where F is degenerate, inverted or
-        // the criteria of the scene ask for it
         const bool use64 = !(J > 0.f) || (fabsf(J) < s.j_tol) || (smin < s.cond_tol * smax) ||
                            (gap < s.gap_tol * smax);
         if (use64) {
-          double Fd[9], taud[9], sgd[3];
+          const unsigned long long slot = atomicAdd(v.fp64_count, 1ull);
+          v.fp64_list[slot] = t;
 #pragma unroll
-          for (int q = 0; q < 9; ++q) Fd[q] = (double)F[q];
-          constitutive<double>(mt.model, Fd, (double)mu, (double)lam, (double)mt.alpha, taud, sgd);
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            F[q] = (float)Fd[q];
-            tau[q] = (float)taud[q];
-          }
-          atomicAdd(v.fp64_count, 1ull);
+          for (int q = 0; q < 9; ++q) tau[q] = 0.f;
         } else {
-          float so[3];
-          constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, so, U, sg);
+          constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, U, e, sg);
         }
       }
       // M' = m B' - dt V0 tau, B' = dx Bh
@@ -651,6 +644,53 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
     }
     __syncthreads();  // the next chunk (or block) overwrites the staged copies
     }
+  }
+}
+
+// Float64 pass of the precision extension: the particles G2P listed (F
+// degenerate, inverted or flagged by the scene's criteria) get the full
+// rotation-variant SVD and constitutive update in float64.  G2P stored the
+// advanced F' and M = m B'; this pass stores the projected F and subtracts
+// dt V0 tau from M.  Grid-stride over the list; an empty list returns at once.
+__global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
+  const uint32_t n = (uint32_t)min(*v.fp64_count, (unsigned long long)v.n_cur);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = v.fp64_list[i];
+    const float4 X = v.nxt.X[t];
+    const MatDev mt = v.mats[__float_as_uint(X.w)];
+    const SceneDev s = v.scenes[mt.scene];
+    double mu = mt.mu, lam = mt.lam;
+    if (v.nxt.E) {
+      const double E = v.nxt.E[t], nu = mt.nu;
+      mu = E / (2.0 * (1.0 + nu));
+      lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    }
+    const float4 f0 = v.nxt.F0[t], f1 = v.nxt.F1[t];
+    double F[9] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, v.nxt.F2[t]};
+    double tau[9], sg[3];
+    constitutive<double>(mt.model, F, mu, lam, (double)mt.alpha, tau, sg);
+    const double dtv = (double)s.dt * (double)s.V0;
+    float4 a = v.nxt.VM0[t], b = v.nxt.VM1[t], c = v.nxt.VM2[t];
+    a.w = (float)(a.w - dtv * tau[0]);
+    b = make_float4((float)(b.x - dtv * tau[1]), (float)(b.y - dtv * tau[2]), (float)(b.z - dtv * tau[3]),
+                    (float)(b.w - dtv * tau[4]));
+    c = make_float4((float)(c.x - dtv * tau[5]), (float)(c.y - dtv * tau[6]), (float)(c.z - dtv * tau[7]),
+                    (float)(c.w - dtv * tau[8]));
+    float Ff[9];
+    bool fin = isfinite(a.w) && isfinite(b.x) && isfinite(b.y) && isfinite(b.z) && isfinite(b.w) &&
+               isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      Ff[q] = (float)F[q];
+      fin = fin && isfinite(Ff[q]);
+    }
+    if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
+    v.nxt.VM0[t] = a;
+    v.nxt.VM1[t] = b;
+    v.nxt.VM2[t] = c;
+    v.nxt.F0[t] = make_float4(Ff[0], Ff[1], Ff[2], Ff[3]);
+    v.nxt.F1[t] = make_float4(Ff[4], Ff[5], Ff[6], Ff[7]);
+    v.nxt.F2[t] = Ff[8];
   }
 }
 
@@ -915,8 +955,8 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
     case LK_P2G: k_p2g<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
     case LK_UPDATE: k_grid_update<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
     case LK_G2P:
-      // register budget of G2P: 4 CTAs/SM (128 registers) by default; the
-      // CKMPM_G2P_MINB environment variable selects 5 or 6 (102 / 85)
+      // register budget of G2P: 4 CTAs/SM (128 registers) by default; 5 or
+      // 6 (96 / 80 registers, no spills either) on request: measured slower
       if (lc.g2p_minb >= 6)
         k_g2p<KIND, 6><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
       else if (lc.g2p_minb == 5)
@@ -924,6 +964,7 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
       else
         k_g2p<KIND, 4><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
       break;
+    case LK_G2P_FP64: k_g2p_fp64<<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
   }
 }

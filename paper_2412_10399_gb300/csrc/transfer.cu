@@ -55,6 +55,18 @@ __device__ __forceinline__ float sin_2pi(float f) {
   return t * p;
 }
 
+// 1/x for a normal float x: the hardware approximation refined by one
+// Newton-Raphson step e = 1 - x y, y <- y + y e (the classical iteration for
+// the reciprocal; the error after one step is about the square of the
+// approximation's, below one ulp).  No special-case branches: callers pass
+// values bounded away from 0 and infinity.
+__device__ __forceinline__ float rcp_nr(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  const float e = fmaf(-x, y, 1.0f);
+  return fmaf(y, e, y);
+}
+
 template <int KIND>
 struct Geo;
 template <>
@@ -155,9 +167,10 @@ struct Sten<0> {
       lam[a] = 0.5f * (m2p + m2m) - sg * sg;
       s[a] = sg;
     }
-    float li[3] = {__frcp_rn(lam[0]), __frcp_rn(lam[1]), __frcp_rn(lam[2])};
+    // Lambda_a in [0.0826, 0.1586] and 1 + s^T Lambda^-1 s in [1, 1.3]
+    float li[3] = {rcp_nr(lam[0]), rcp_nr(lam[1]), rcp_nr(lam[2])};
     float y[3] = {li[0] * s[0], li[1] * s[1], li[2] * s[2]};
-    float den = __frcp_rn(1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
+    float den = rcp_nr(1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -224,6 +237,95 @@ __device__ __forceinline__ void for_nodes(const Sten<1>& st, Fn&& fn) {
 #pragma unroll
       for (int sx = 0; sx < 3; ++sx) fn(row + sx, st.w[0][sx] * wyz, st.d[0][sx], st.d[1][sy], st.d[2][sz]);
     }
+}
+
+// G2P gather as a tensor-product contraction (a node's weight is the product
+// of per-axis weights): over one grid's N^3 stencil, S = sum w v~ and the
+// first moments M_a = sum w v~ s_a (s_a in 0..N-1: the node's offset in the
+// stencil along axis a), reducing x, then y, then z.  With x_i - x_p =
+// (s - f) dx per axis, sum w v~ (x_i - x_p)_a / dx = M_a - f_a S.  sv holds
+// the staged nodes with row pitch E; base is the stencil's first node.
+template <int N, int E>
+__device__ __forceinline__ void gather_moments(const float4* sv, int base, const float* wx, const float* wy,
+                                               const float* wz, float* S, float* Mx, float* My, float* Mz) {
+#pragma unroll
+  for (int sz = 0; sz < N; ++sz) {
+    float Ps[3], Px[3], Py[3];
+#pragma unroll
+    for (int sy = 0; sy < N; ++sy) {
+      float Rs[3], Rx[3];
+      const int row = base + (sz * E + sy) * E;
+#pragma unroll
+      for (int sx = N - 1; sx >= 0; --sx) {
+        const float4 a = sv[row + sx];
+        const float t[3] = {wx[sx] * a.x, wx[sx] * a.y, wx[sx] * a.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (sx == N - 1) {
+            Rs[c] = t[c];
+            Rx[c] = (float)sx * t[c];
+          } else {
+            Rs[c] += t[c];
+            if (sx > 0) Rx[c] = fmaf((float)sx, t[c], Rx[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float u = wy[sy] * Rs[c];
+        if (sy == 0) {
+          Ps[c] = u;
+          Px[c] = wy[sy] * Rx[c];
+        } else {
+          Ps[c] += u;
+          Px[c] = fmaf(wy[sy], Rx[c], Px[c]);
+          Py[c] = sy == 1 ? u : fmaf((float)sy, u, Py[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float u = wz[sz] * Ps[c];
+      if (sz == 0) {
+        S[c] = u;
+        Mx[c] = wz[sz] * Px[c];
+        My[c] = wz[sz] * Py[c];
+      } else {
+        S[c] += u;
+        Mx[c] = fmaf(wz[sz], Px[c], Mx[c]);
+        My[c] = fmaf(wz[sz], Py[c], My[c]);
+        Mz[c] = sz == 1 ? u : fmaf((float)sz, u, Mz[c]);
+      }
+    }
+  }
+}
+
+// v = h sum w v~ and Bh = h sum w v~ (x_i - x_p)^T / dx (row c, column a) over
+// the particle's stencil; h = 1/2 averages the two CK grids.
+__device__ __forceinline__ void g2p_gather(const Sten<0>& st, const float4* sv, float* vel, float* Bh) {
+  float S[2][3], M[2][3][3];
+  gather_moments<2, 5>(sv, (st.r[0][2] * 5 + st.r[0][1]) * 5 + st.r[0][0], st.w[0][0], st.w[0][1], st.w[0][2],
+                       S[0], M[0][0], M[0][1], M[0][2]);
+  gather_moments<2, 6>(sv, 125 + (st.r[1][2] * 6 + st.r[1][1]) * 6 + st.r[1][0], st.w[1][0], st.w[1][1],
+                       st.w[1][2], S[1], M[1][0], M[1][1], M[1][2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vel[c] = 0.5f * (S[0][c] + S[1][c]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)  // f_a = -d[g][a][0]
+      Bh[c * 3 + a] = 0.5f * (fmaf(st.d[0][a][0], S[0][c], M[0][a][c]) + fmaf(st.d[1][a][0], S[1][c], M[1][a][c]));
+  }
+}
+
+__device__ __forceinline__ void g2p_gather(const Sten<1>& st, const float4* sv, float* vel, float* Bh) {
+  float S[3], M[3][3];
+  gather_moments<3, 6>(sv, (st.r[2] * 6 + st.r[1]) * 6 + st.r[0], st.w[0], st.w[1], st.w[2], S, M[0], M[1], M[2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vel[c] = S[c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Bh[c * 3 + a] = fmaf(st.d[a][0], S[c], M[a][c]);
+  }
 }
 
 template <int KIND>
@@ -488,8 +590,8 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
     __syncthreads();
     for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
     const uint32_t m = min(cnt - c0, (uint32_t)CAP);
-    // the chunk's particle state: cp.async gathers through the binned order,
-    // all in flight while the grid velocities are staged
+    // the chunk's particle state and (first chunk) the block's grid
+    // velocities: cp.async gathers, all in flight before the one wait
 #pragma unroll 4
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
       const uint32_t p = v.perm[start + c0 + i];
@@ -505,7 +607,10 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
         int g, lx, ly, lz;
         staged_coords<KIND>(j, g, lx, ly, lz);
         long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
-        sv[j] = gi >= 0 ? v.Gvel[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gi >= 0)
+          cp_async16(&sv[j], &v.Gvel[gi]);
+        else
+          sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     cp_async_wait_all();
@@ -531,26 +636,9 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
         flag_error(v.err, CK_ERR_INTERNAL);
         continue;
       }
-      float vx = 0.f, vy = 0.f, vz = 0.f;
-      float Bh[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) Bh[q] = 0.f;
-      for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
-        const float4 g4 = sv[j];
-        float gx = g4.x * w, gy = g4.y * w, gz = g4.z * w;
-        vx += gx;
-        vy += gy;
-        vz += gz;
-        Bh[0] += gx * dx; Bh[1] += gx * dy; Bh[2] += gx * dz;
-        Bh[3] += gy * dx; Bh[4] += gy * dy; Bh[5] += gy * dz;
-        Bh[6] += gz * dx; Bh[7] += gz * dy; Bh[8] += gz * dz;
-      });
-      const float h = Geo<KIND>::half;
-      vx *= h;
-      vy *= h;
-      vz *= h;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) Bh[q] *= h;
+      float vel[3], Bh[9];
+      g2p_gather(st, sv, vel, Bh);
+      const float vx = vel[0], vy = vel[1], vz = vel[2];
       float Di[9];
       dinv_of<KIND>(st, Di);
       // C = B D^-1 = Bh Di / dx ; F' = (I + dt C) F

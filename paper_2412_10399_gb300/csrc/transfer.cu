@@ -356,9 +356,9 @@ __device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, in
 // Shared-memory accumulation is in 32-bit fixed point: integer shared
 // atomics run about 4x faster than float ones on this part (measured), and
 // integer sums do not depend on the order of the atomics.  A first pass over
-// the block's particles bounds every contribution each can make (p2g_bound:
-// |w| <= 1, offsets at most dmax cells, rows of D^-1 summing to at most 14.5
-// cells^-2), so with cnt particles no node sum can exceed cnt times the
+// the block's particles bounds every contribution each can make (p2g_bound,
+// from the largest weight, weight times offset and row sum of D^-1 of the
+// stencil), so with cnt particles no node sum can exceed cnt times the
 // block's largest bound, and the scale maps that to 2^30 (no overflow).
 // Rounding costs at most half a unit per contribution, cnt * bound * 2^-31.
 
@@ -373,32 +373,42 @@ struct P2GPart {
   float4 X, a, b, c;
 };
 
-// Largest row abs-sum of D^-1 over all particle positions, in cells^-2: 14.04
-// for the CK dual grid (evaluated over a 121^3 grid of fractions; 14.5 keeps
-// a margin) and 4 for the quadratic B-spline (D^-1 = 4 I).
+// Per-stencil bounds of one P2G contribution w (m v + A^ d) (d: node offset
+// in cells); wmax and the product wd * dinv keep a margin of at least 0.3%
+// over the exact maxima for float rounding:
+//   wmax  largest node weight: CK 1 (K1(0)); quadratic 0.75^3;
+//   wd    largest |w d_a|: max over one axis of |d| K(|d|) times the largest
+//         weight of the other two: CK 0.27751 (at |d| = 0.394) x 1;
+//         quadratic 0.25 (at |d| = 1/2) x 0.75^2 = 0.140625;
+//   dinv  largest row abs-sum of D^-1 in cells^-2: CK 14.04 (over a 121^3
+//         grid of fractions), quadratic 4 (D^-1 = 4 I).
 template <int KIND>
-struct DinvRowBound;
+struct P2GBound;
 template <>
-struct DinvRowBound<0> {
-  static constexpr float value = 14.5f;
-  static constexpr float dmax = 1.0f;  // |x_i - x_p| per axis, cells
+struct P2GBound<0> {
+  static constexpr float wmax = 1.003f;
+  static constexpr float wd = 0.2785f;
+  static constexpr float dinv = 14.5f;
 };
 template <>
-struct DinvRowBound<1> {
-  static constexpr float value = 4.0f;
-  static constexpr float dmax = 1.5f;
+struct P2GBound<1> {
+  static constexpr float wmax = 0.4232f;
+  static constexpr float wd = 0.1411f;
+  static constexpr float dinv = 4.0f;
 };
 
-// Bound of |w (m v + A^ d)|_inf for every node a particle touches (|w| <= 1):
-// m |v|_inf + dmax * max_row sum_k |M_rk| * max_row sum_j |D^-1| / dx.
+// Bound of |w (m v + A^ d)|_inf over every node a particle touches:
+// wmax m |v|_inf + wd * dinv * max_row sum_k |M_rk| / dx, since
+// |w (A^ d)_r| <= sum_k |A^_rk| |w d_k| and the rows of A^ = M D^-1 / dx sum
+// to at most sum_j |M_rj| * dinv / dx.
 template <int KIND>
 __device__ __forceinline__ float p2g_bound(const SceneDev& s, float mass, const P2GPart& q) {
   const float r0 = fabsf(q.a.w) + fabsf(q.b.x) + fabsf(q.b.y);
   const float r1 = fabsf(q.b.z) + fabsf(q.b.w) + fabsf(q.c.x);
   const float r2 = fabsf(q.c.y) + fabsf(q.c.z) + fabsf(q.c.w);
   const float rm = fmaxf(r0, fmaxf(r1, r2));
-  return mass * fmaxf(fabsf(q.a.x), fmaxf(fabsf(q.a.y), fabsf(q.a.z))) +
-         DinvRowBound<KIND>::dmax * DinvRowBound<KIND>::value * rm * s.inv_dx;
+  return P2GBound<KIND>::wmax * mass * fmaxf(fabsf(q.a.x), fmaxf(fabsf(q.a.y), fabsf(q.a.z))) +
+         P2GBound<KIND>::wd * P2GBound<KIND>::dinv * rm * s.inv_dx;
 }
 
 template <int KIND>
@@ -478,7 +488,7 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
       }
       const float mass = v.mats[__float_as_uint(q.X.w)].mass;
       bmom = fmaxf(bmom, p2g_bound<KIND>(s, mass, q));
-      bmass = fmaxf(bmass, mass);
+      bmass = fmaxf(bmass, P2GBound<KIND>::wmax * mass);
     }
     for (int o = 16; o > 0; o >>= 1) {
       bmass = fmaxf(bmass, __shfl_xor_sync(0xffffffffu, bmass, o));

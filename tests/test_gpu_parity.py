@@ -62,6 +62,29 @@ def test_p2g_grid_parity(kernel, model, n, res, seed):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+def test_p2g_grid_parity_dense_blocks(kernel):
+    """8 particles per cell over cells [8, 24)^3: 64 particle blocks hold about
+    512 particles each, so P2G takes its large-block fixed-point path."""
+    ck = need_gpu()
+    sc, B, F = random_scene(32768, 32, 4, model=S.DRUCKER_PRAGER, kernel=kernel, f_scale=0.08, box=(8.0, 24.0))
+    sim = _sim(ck, sc, B, F)
+    sim.probe_grids()
+    gm = sim.read(ck.FIELD_GRID_M)
+    gp = sim.read(ck.FIELD_GRID_P)
+    st = sim.stats()
+    sim.close()
+    assert st.n_particle_blocks >= 64
+    prm = O.params_from_scene(sc)
+    grids = O.p2g(oracle_state(sc, B, F), prm)
+    nn = sc.res + 1
+    for gi, k in enumerate(O.grid_ids(kernel)):
+        mo = grids[k][0].numpy().reshape(nn, nn, nn)
+        po = grids[k][1].numpy().reshape(nn, nn, nn, 3)
+        assert rel(gm[gi], mo) <= 1e-5, f"grid {k} mass"
+        assert rel(gp[gi], po) <= 1e-5, f"grid {k} momentum"
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("model", MODELS)
 def test_one_step_particle_parity(kernel, model):
     ck = need_gpu()

@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(1024) k_scan_top(StepView v, BinScratch bs, ui
     carry_n = 0;
     *v.n_g = 0;
     *v.fp64_count = 0ull;
+    v.work[0] = 0u;
+    v.work[1] = 0u;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -97,6 +97,7 @@ struct StepView {
   uint32_t* err;
   unsigned long long* fp64_count;  // particles listed for the float64 pass this step
   uint32_t* fp64_list;  // their slots in nxt (capacity: the pool)
+  uint32_t* work;       // [0] next P2G block, [1] next G2P block (dynamic scheduling)
   uint32_t n_keys;      // size of the key space
   uint32_t n_cur;       // particles in cur (including dead ones)
   uint32_t keep_gacc;   // grid update leaves Gacc in place (probe)

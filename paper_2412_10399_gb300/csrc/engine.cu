@@ -100,7 +100,7 @@ struct ckmpm_ctx {
   uint32_t* key[2]{};
   uint32_t* cnt[2]{};
   uint32_t *offset = nullptr, *cursor = nullptr, *perm = nullptr, *pb_key = nullptr, *pb_scene = nullptr;
-  uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit)
+  uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit), [6..7] work
   uint32_t* fp64_list = nullptr;  // particles of the float64 pass (capacity cap_n)
   uint32_t *gflag = nullptr, *table = nullptr, *g_list = nullptr, *g_scene = nullptr;
   uint32_t *tile_cnt = nullptr, *tile_ne = nullptr, *scene_tab = nullptr;
@@ -215,6 +215,7 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.err = ctx->counters + 2;
   v.fp64_count = (unsigned long long*)(ctx->counters + 4);
   v.fp64_list = ctx->fp64_list;
+  v.work = ctx->counters + 6;
   v.gflag = ctx->gflag;
   v.table = ctx->table;
   v.pool_cap = (uint32_t)ctx->cap_pool;

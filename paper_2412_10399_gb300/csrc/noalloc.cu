@@ -143,6 +143,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   v.n_g = counters + 1;
   v.err = counters + 2;
   v.fp64_count = (unsigned long long*)(counters + 4);
+  v.work = counters + 6;
   v.gflag = cv.take<uint32_t>(nvb);
   v.table = cv.take<uint32_t>(nvb);
   v.g_list = cv.take<uint32_t>(nvb);

@@ -448,9 +448,16 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
   __shared__ float4 sX[kP2GStage], sA[kP2GStage], sB[kP2GStage], sC[kP2GStage];
   __shared__ uint32_t bslot[8];
   __shared__ float sred[2][4];
+  __shared__ uint32_t s_bi;
   const uint32_t npb = *v.n_pb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
+  for (;;) {
+    // dynamic scheduling: one block at a time from a counter; the barrier at
+    // the end of the previous block keeps s_bi from being overwritten early
+    if (threadIdx.x == 0) s_bi = atomicAdd(&v.work[0], 1u);
+    __syncthreads();
+    const uint32_t bi = s_bi;
+    if (bi >= npb) break;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
@@ -577,10 +584,15 @@ __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
 
 __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(a, fminf(b, c)); }
 
-constexpr int kG2PStage = 512;  // particles staged per chunk
+// G2P runs one warp per CTA: a particle block's ~400-500 particles leave a
+// partly idle last round on 32 lanes instead of on 128, and the staging
+// waits are warp-level, so a lane that finishes early never holds up three
+// other warps at a block barrier.  MINB counts 4-warp equivalents per SM.
+constexpr int kG2PWarp = 32;
+constexpr int kG2PStage = 128;  // particles staged per chunk
 
 template <int KIND, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
+__global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   constexpr int CAP = kG2PStage;
   __shared__ float4 sv[NS];  // staged v~ (w unused): one 16-byte shared load per node
@@ -589,7 +601,13 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
   __shared__ uint32_t sID[CAP];
   __shared__ uint32_t bslot[8];
   const uint32_t npb = *v.n_pb;
-  for (uint32_t bi = blockIdx.x; bi < npb; bi += gridDim.x) {
+  for (;;) {
+    // blocks are handed out one at a time (dynamic scheduling: block costs
+    // vary with their particle counts and constitutive work)
+    uint32_t bi = 0;
+    if (threadIdx.x == 0) bi = atomicAdd(&v.work[1], 1u);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    if (bi >= npb) break;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
@@ -597,7 +615,7 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
-    __syncthreads();
+    __syncwarp();
     for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
     const uint32_t m = min(cnt - c0, (uint32_t)CAP);
     // the chunk's particle state and (first chunk) the block's grid
@@ -624,7 +642,7 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
       }
     }
     cp_async_wait_all();
-    __syncthreads();
+    __syncwarp();
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
       const uint32_t t = start + c0 + i;
       const float4 X = sX[i];
@@ -740,7 +758,7 @@ __global__ void __launch_bounds__(128, MINB) k_g2p(StepView v) {
       v.key_nxt[t] = nk;
       warp_aggregated_inc(v.cnt_nxt, nk);
     }
-    __syncthreads();  // the next chunk (or block) overwrites the staged copies
+    __syncwarp();  // the next chunk (or block) overwrites the staged copies
     }
   }
 }
@@ -1053,14 +1071,15 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
     case LK_P2G: k_p2g<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
     case LK_UPDATE: k_grid_update<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
     case LK_G2P:
-      // register budget of G2P: 4 CTAs/SM (128 registers) by default; 5 or
-      // 6 (96 / 80 registers, no spills either) on request: measured slower
+      // register budget of G2P: 16 warps/SM (128 registers) by default; 20
+      // or 24 (96 / 80 registers, no spills either) on request: measured
+      // slower.  One resident wave of one-warp CTAs.
       if (lc.g2p_minb >= 6)
-        k_g2p<KIND, 6><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
+        k_g2p<KIND, 6><<<lc.sm_count * 24, kG2PWarp, 0, lc.stream>>>(v);
       else if (lc.g2p_minb == 5)
-        k_g2p<KIND, 5><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
+        k_g2p<KIND, 5><<<lc.sm_count * 20, kG2PWarp, 0, lc.stream>>>(v);
       else
-        k_g2p<KIND, 4><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v);
+        k_g2p<KIND, 4><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
       break;
     case LK_G2P_FP64: k_g2p_fp64<<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;

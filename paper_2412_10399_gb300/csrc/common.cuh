@@ -78,6 +78,9 @@ struct StepView {
   uint32_t* key_nxt;    // keys written by G2P for nxt
   uint32_t* cnt_cur;    // histogram of key_cur over the key space
   uint32_t* cnt_nxt;    // histogram written by G2P
+  uint32_t* bnd_cur;    // per key: P2G contribution bounds (mass, momentum) of cur, float
+                        // bits; P2G clears an active block's pair after use
+  uint32_t* bnd_nxt;    // the same for nxt, written by G2P (all zero before it)
   uint32_t* offset;     // exclusive scan of cnt_cur
   uint32_t* cursor;     // scatter cursors
   uint32_t* perm;       // sorted slot -> index into cur
@@ -100,7 +103,7 @@ struct StepView {
   uint32_t* work;       // [0] next P2G block, [1] next G2P block (dynamic scheduling)
   uint32_t n_keys;      // size of the key space
   uint32_t n_cur;       // particles in cur (including dead ones)
-  uint32_t keep_gacc;   // grid update leaves Gacc in place (probe)
+  uint32_t keep_gacc;   // probe: the grid update leaves Gacc, P2G keeps bnd_cur
 };
 
 __device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }
@@ -171,6 +174,24 @@ __device__ __forceinline__ uint32_t warp_aggregated_inc(uint32_t* counters, uint
   if (lane == leader) base = atomicAdd(&counters[key], (uint32_t)__popc(peers));
   base = __shfl_sync(peers, base, leader);
   return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// Histogram increment and P2G contribution bounds of particles binned under
+// `key` (lanes with equal keys add once).  The bounds are non-negative floats
+// kept as bit patterns (whose unsigned order is the float order); each warp
+// contributes the largest bound over all its active lanes, which may only
+// overestimate a block's bound.
+__device__ __forceinline__ void warp_aggregated_bin(uint32_t* cnt, uint32_t* bnd, uint32_t key, float bmass,
+                                                    float bmom) {
+  const unsigned mask = __activemask();
+  const uint32_t bm = __reduce_max_sync(mask, __float_as_uint(bmass));
+  const uint32_t bp = __reduce_max_sync(mask, __float_as_uint(bmom));
+  const unsigned peers = __match_any_sync(mask, key);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+    atomicAdd(&cnt[key], (uint32_t)__popc(peers));
+    atomicMax(&bnd[2 * key], bm);
+    atomicMax(&bnd[2 * key + 1], bp);
+  }
 }
 
 __device__ __forceinline__ bool finite4(float4 a) {

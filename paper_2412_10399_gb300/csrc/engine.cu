@@ -99,6 +99,7 @@ struct ckmpm_ctx {
   int cur = 0;
   uint32_t* key[2]{};
   uint32_t* cnt[2]{};
+  uint32_t* bnd[2]{};  // per key: P2G contribution bounds (2 floats as bits)
   uint32_t *offset = nullptr, *cursor = nullptr, *perm = nullptr, *pb_key = nullptr, *pb_scene = nullptr;
   uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit), [6..7] work
   uint32_t* fp64_list = nullptr;  // particles of the float64 pass (capacity cap_n)
@@ -205,6 +206,8 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.key_nxt = ctx->key[ctx->cur ^ 1];
   v.cnt_cur = ctx->cnt[ctx->cur];
   v.cnt_nxt = ctx->cnt[ctx->cur ^ 1];
+  v.bnd_cur = ctx->bnd[ctx->cur];
+  v.bnd_nxt = ctx->bnd[ctx->cur ^ 1];
   v.offset = ctx->offset;
   v.cursor = ctx->cursor;
   v.perm = ctx->perm;
@@ -426,7 +429,8 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
             alloc_n(ctx, ctx->key[0], ctx->cap_n) && alloc_n(ctx, ctx->key[1], ctx->cap_n) &&
             alloc_n(ctx, ctx->perm, ctx->cap_n) && alloc_n(ctx, ctx->fp64_list, ctx->cap_n) &&
             alloc_n(ctx, ctx->cnt[0], ctx->cap_keys) &&
-            alloc_n(ctx, ctx->cnt[1], ctx->cap_keys) && alloc_n(ctx, ctx->offset, ctx->cap_keys) &&
+            alloc_n(ctx, ctx->cnt[1], ctx->cap_keys) && alloc_n(ctx, ctx->bnd[0], 2 * ctx->cap_keys) &&
+            alloc_n(ctx, ctx->bnd[1], 2 * ctx->cap_keys) && alloc_n(ctx, ctx->offset, ctx->cap_keys) &&
             alloc_n(ctx, ctx->cursor, ctx->cap_keys) && alloc_n(ctx, ctx->pb_key, ctx->cap_keys) &&
             alloc_n(ctx, ctx->pb_scene, ctx->cap_keys) && alloc_n(ctx, ctx->counters, 8) &&
             alloc_n(ctx, ctx->gflag, ctx->cap_vblocks) && alloc_n(ctx, ctx->table, ctx->cap_vblocks) &&
@@ -440,6 +444,8 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   if (!ok) return fail(ctx, CKMPM_ENOMEM, "device memory allocation failed");
   CK_TRY(cudaMemsetAsync(ctx->cnt[0], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->cnt[1], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->bnd[0], 0, sizeof(uint32_t) * 2 * ctx->cap_keys, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->bnd[1], 0, sizeof(uint32_t) * 2 * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->counters, 0, sizeof(uint32_t) * 8, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->gflag, 0, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->table, 0xff, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
@@ -479,8 +485,10 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   }
   if (ctx->keys_dirty) {
     CK_TRY(cudaMemsetAsync(ctx->cnt[ctx->cur], 0, sizeof(uint32_t) * v.n_keys, ctx->stream), "memset");
+    CK_TRY(cudaMemsetAsync(ctx->bnd[ctx->cur], 0, sizeof(uint32_t) * 2 * v.n_keys, ctx->stream), "memset");
     if (ctx->n_cur > 0)
       ck::launch_rekey(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur],
+                       ctx->bnd[ctx->cur],
                        ctx->d_scenes, ctx->d_mats, (uint32_t)ctx->n_cur, v.err);
     ctx->keys_dirty = false;
   }
@@ -511,10 +519,10 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   tbeg(ctx, ep, 5);
   ck::launch_bin(ctx->stream, v, bs, ck::LB_GLIST, ngb, grid_ctas);
   tend(ctx, ep);
+  v.keep_gacc = probe ? 1u : 0u;
   tbeg(ctx, ep, 2);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_P2G);
   tend(ctx, ep);
-  v.keep_gacc = probe ? 1u : 0u;
   tbeg(ctx, ep, 3);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_UPDATE);
   tend(ctx, ep);
@@ -661,8 +669,8 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
     if (!dE) return fail(ctx, CKMPM_ENOMEM, "allocation failed");
     CK_TRY(cudaMemcpyAsync(dE, Ehost.data(), sizeof(float) * sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload E");
   }
-  ck::launch_admit(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur], ctx->d_scenes,
-                   slot, (uint32_t)mb, (uint32_t)sc->n_materials, (uint32_t)ctx->n_cur, (uint32_t)sc->n, dx_, dv_, dm_, dE,
+  ck::launch_admit(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur],
+                   ctx->bnd[ctx->cur], ctx->d_scenes, ctx->d_mats, slot, (uint32_t)mb, (uint32_t)sc->n_materials, (uint32_t)ctx->n_cur, (uint32_t)sc->n, dx_, dv_, dm_, dE,
                    ctx->counters + 2);
   CK_TRY(cudaGetLastError(), "admit launch");
   if (dE) {
@@ -769,6 +777,8 @@ ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id) {
     }
   }
   CK_TRY(cudaMemsetAsync(ctx->cnt[ctx->cur] + h.key_base, 0, sizeof(uint32_t) * h.nkeys, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->bnd[ctx->cur] + 2 * h.key_base, 0, sizeof(uint32_t) * 2 * h.nkeys, ctx->stream),
+         "memset");
   h.alive = false;
   ctx->h_scenes[scene_id].alive = 0;
   CK_TRY(cudaMemcpyAsync(ctx->d_scenes + scene_id, &ctx->h_scenes[scene_id], sizeof(SceneDev), cudaMemcpyHostToDevice,
@@ -888,7 +898,9 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (tmp) dev_free(ctx, tmp);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
-  if (field == CKMPM_FIELD_X) ctx->keys_dirty = true;
+  // keys (positions) or P2G bounds (velocity, M through B, F or E) changed:
+  // the next step re-bins the pool first
+  ctx->keys_dirty = true;
   return read_device_error(ctx);
 }
 

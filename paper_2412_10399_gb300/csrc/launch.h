@@ -24,11 +24,12 @@ void launch_read_particles(int kind, cudaStream_t st, Pool P, const SceneDev* sc
 void launch_write_particles(cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
                             uint32_t start, uint32_t n, int field, const float* in);
 void launch_read_grid(int kind, cudaStream_t st, const StepView& v, int scene, int which, float* out);
-void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene,
-                  uint32_t mat_base, uint32_t nmat, uint32_t start, uint32_t n, const float* x, const float* v,
-                  const uint8_t* mat, const float* E, uint32_t* err);
-void launch_rekey(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes,
-                  const MatDev* mats, uint32_t n, uint32_t* err);
+void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd,
+                  const SceneDev* scenes, const MatDev* mats, int scene, uint32_t mat_base, uint32_t nmat,
+                  uint32_t start, uint32_t n, const float* x, const float* v, const uint8_t* mat, const float* E,
+                  uint32_t* err);
+void launch_rekey(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd,
+                  const SceneDev* scenes, const MatDev* mats, uint32_t n, uint32_t* err);
 
 // bin.cu
 constexpr int kScanTile = 4096;  // keys per scan tile

@@ -133,6 +133,8 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   v.key_nxt = v.key_cur;
   v.cnt_cur = cv.take<uint32_t>(nkeys);
   v.cnt_nxt = cv.take<uint32_t>(nkeys);
+  v.bnd_cur = cv.take<uint32_t>(2 * nkeys);
+  v.bnd_nxt = cv.take<uint32_t>(2 * nkeys);
   v.offset = cv.take<uint32_t>(nkeys);
   v.cursor = cv.take<uint32_t>(nkeys);
   v.perm = cv.take<uint32_t>(n);
@@ -214,6 +216,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   CK_S(cudaMemcpyAsync(scene_tab, tab, sizeof(tab), cudaMemcpyHostToDevice, st));
   // everything a previous call may have left behind and the kernels expect zero
   CK_S(cudaMemsetAsync(v.cnt_cur, 0, sizeof(uint32_t) * nkeys, st));
+  CK_S(cudaMemsetAsync(v.bnd_cur, 0, sizeof(uint32_t) * 2 * nkeys, st));
   CK_S(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 8, st));
   CK_S(cudaMemsetAsync(v.gflag, 0, sizeof(uint32_t) * nvb, st));
   CK_S(cudaMemsetAsync(v.Gacc, 0, sizeof(float4) * nvb * NG * ck::kBlockNodes, st));
@@ -221,10 +224,16 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   CK_S(cudaMemsetAsync(grid_p, 0, sizeof(float) * 3 * NG * nn, st));
 
   // particles: x, v, material; B = 0 and F = I, then the caller's F and B
-  ck::launch_admit(kernel, st, P, v.key_cur, v.cnt_cur, d_scene, 0, 0u, (uint32_t)sc->n_materials, 0u, (uint32_t)n,
-                   sc->x, sc->v, sc->mat, nullptr, v.err);
-  if (F) ck::launch_write_particles(st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_F, F);
-  if (B) ck::launch_write_particles(st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_B, B);
+  ck::launch_admit(kernel, st, P, v.key_cur, v.cnt_cur, v.bnd_cur, d_scene, d_mats, 0, 0u, (uint32_t)sc->n_materials,
+                   0u, (uint32_t)n, sc->x, sc->v, sc->mat, nullptr, v.err);
+  if (F || B) {
+    if (F) ck::launch_write_particles(st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_F, F);
+    if (B) ck::launch_write_particles(st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_B, B);
+    // M changed: histogram and P2G bounds again
+    CK_S(cudaMemsetAsync(v.cnt_cur, 0, sizeof(uint32_t) * nkeys, st));
+    CK_S(cudaMemsetAsync(v.bnd_cur, 0, sizeof(uint32_t) * 2 * nkeys, st));
+    ck::launch_rekey(kernel, st, P, v.key_cur, v.cnt_cur, v.bnd_cur, d_scene, d_mats, (uint32_t)n, v.err);
+  }
   // binning and P2G, as in a context's step
   const int grid_ctas = sms * 4;
   ck::launch_bin(st, v, bs, ck::LB_SCAN_TILES, (uint32_t)nvb, grid_ctas);

@@ -362,12 +362,13 @@ __device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, in
 // block's largest bound, and the scale maps that to 2^30 (no overflow).
 // Rounding costs at most half a unit per contribution, cnt * bound * 2^-31.
 
-// Particles of a block with at most kP2GStage particles are copied into
-// shared memory up front (cp.async gathers through the binned order, all in
-// flight together) and read back by both passes; the scatter pass takes them
-// C apart per lane with C odd, so each quarter-warp's 16-byte reads fall on
-// distinct bank groups.
-constexpr int kP2GStage = 544;  // 17 * 32
+// P2G runs one warp per CTA and streams a block's particles through shared
+// memory in chunks of kP2GStage (cp.async gathers through the binned order,
+// all in flight together); lanes take a chunk's particles C = kP2GStage / 32
+// apart (C odd), so each quarter-warp's 16-byte reads fall on distinct bank
+// groups and neighbouring lanes come from different cells.
+constexpr int kP2GWarp = 32;
+constexpr int kP2GStage = 96;  // 3 * 32
 
 struct P2GPart {
   float4 X, a, b, c;
@@ -401,14 +402,20 @@ struct P2GBound<1> {
 // wmax m |v|_inf + wd * dinv * max_row sum_k |M_rk| / dx, since
 // |w (A^ d)_r| <= sum_k |A^_rk| |w d_k| and the rows of A^ = M D^-1 / dx sum
 // to at most sum_j |M_rj| * dinv / dx.
+// The particle's two bounds (mass, momentum) go into its block's entry of
+// the per-key bound table when it is binned (G2P for the next step, admission
+// and re-keying otherwise), so P2G reads a block's bounds without a pass over
+// its particles.
 template <int KIND>
-__device__ __forceinline__ float p2g_bound(const SceneDev& s, float mass, const P2GPart& q) {
-  const float r0 = fabsf(q.a.w) + fabsf(q.b.x) + fabsf(q.b.y);
-  const float r1 = fabsf(q.b.z) + fabsf(q.b.w) + fabsf(q.c.x);
-  const float r2 = fabsf(q.c.y) + fabsf(q.c.z) + fabsf(q.c.w);
+__device__ __forceinline__ void p2g_bounds(float inv_dx, float mass, float vx, float vy, float vz, const float* M,
+                                           float& bmass, float& bmom) {
+  const float r0 = fabsf(M[0]) + fabsf(M[1]) + fabsf(M[2]);
+  const float r1 = fabsf(M[3]) + fabsf(M[4]) + fabsf(M[5]);
+  const float r2 = fabsf(M[6]) + fabsf(M[7]) + fabsf(M[8]);
   const float rm = fmaxf(r0, fmaxf(r1, r2));
-  return P2GBound<KIND>::wmax * mass * fmaxf(fabsf(q.a.x), fmaxf(fabsf(q.a.y), fabsf(q.a.z))) +
-         P2GBound<KIND>::wd * P2GBound<KIND>::dinv * rm * s.inv_dx;
+  bmass = P2GBound<KIND>::wmax * mass;
+  bmom = bmass * fmaxf(fabsf(vx), fmaxf(fabsf(vy), fabsf(vz))) +
+         P2GBound<KIND>::wd * P2GBound<KIND>::dinv * rm * inv_dx;
 }
 
 template <int KIND>
@@ -442,94 +449,60 @@ __device__ __forceinline__ void p2g_scatter(const SceneDev& s, const MatDev* mat
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(128) k_p2g(StepView v) {
+__global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  __shared__ int sm[4][NS];
-  __shared__ float4 sX[kP2GStage], sA[kP2GStage], sB[kP2GStage], sC[kP2GStage];
+  constexpr uint32_t CAP = kP2GStage, C = kP2GStage / 32;
+  static_assert(C % 2 == 1, "lane stride must be odd");
+  __shared__ __align__(16) int sm[4][NS];
+  __shared__ float4 sX[CAP], sA[CAP], sB[CAP], sC[CAP];
   __shared__ uint32_t bslot[8];
-  __shared__ float sred[2][4];
-  __shared__ uint32_t s_bi;
   const uint32_t npb = *v.n_pb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x;
   for (;;) {
-    // dynamic scheduling: one block at a time from a counter; the barrier at
-    // the end of the previous block keeps s_bi from being overwritten early
-    if (threadIdx.x == 0) s_bi = atomicAdd(&v.work[0], 1u);
-    __syncthreads();
-    const uint32_t bi = s_bi;
+    // dynamic scheduling: one block at a time from a counter
+    uint32_t bi = 0;
+    if (lane == 0) bi = atomicAdd(&v.work[0], 1u);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
     if (bi >= npb) break;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
     const uint32_t cnt = v.cnt_cur[key];
+    // the block's largest contribution bounds, recorded when its particles
+    // were binned
+    const float bmass = __uint_as_float(v.bnd_cur[2 * key]);
+    const float bmom = __uint_as_float(v.bnd_cur[2 * key + 1]);
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
-    for (int j = threadIdx.x; j < NS; j += blockDim.x) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) sm[c][j] = 0;
-    }
-    const uint32_t C = ((cnt + 31u) >> 5) | 1u;
-    const bool staged = (C << 5) <= (uint32_t)kP2GStage;
-    if (staged) {
-#pragma unroll 4
-      for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const uint32_t p = v.perm[start + i];
-        cp_async16(&sX[i], &v.cur.X[p]);
-        cp_async16(&sA[i], &v.cur.VM0[p]);
-        cp_async16(&sB[i], &v.cur.VM1[p]);
-        cp_async16(&sC[i], &v.cur.VM2[p]);
-      }
-      cp_async_wait_all();
-      __syncthreads();
-    }
-    // pass 1: the largest contribution any particle of the block can make
-    float bmass = 0.f, bmom = 0.f;
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-      P2GPart q;
-      if (staged) {
-        q = P2GPart{sX[i], sA[i], sB[i], sC[i]};
-      } else {
-        const uint32_t p = v.perm[start + i];
-        q = P2GPart{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
-      }
-      const float mass = v.mats[__float_as_uint(q.X.w)].mass;
-      bmom = fmaxf(bmom, p2g_bound<KIND>(s, mass, q));
-      bmass = fmaxf(bmass, P2GBound<KIND>::wmax * mass);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      bmass = fmaxf(bmass, __shfl_xor_sync(0xffffffffu, bmass, o));
-      bmom = fmaxf(bmom, __shfl_xor_sync(0xffffffffu, bmom, o));
-    }
-    if (lane == 0) {
-      sred[0][warp] = bmass;
-      sred[1][warp] = bmom;
-    }
-    __syncthreads();
-    bmass = fmaxf(fmaxf(sred[0][0], sred[0][1]), fmaxf(sred[0][2], sred[0][3]));
-    bmom = fmaxf(fmaxf(sred[1][0], sred[1][1]), fmaxf(sred[1][2], sred[1][3]));
+    for (int j = lane; j < NS; j += kP2GWarp) reinterpret_cast<int4*>(&sm[0][0])[j] = make_int4(0, 0, 0, 0);
     const float fcnt = (float)cnt;
     const float Sm = bmass > 0.f ? 1073741824.0f / (fcnt * bmass) : 1.0f;
     const float Sp = bmom > 0.f ? 1073741824.0f / (fcnt * bmom) : 1.0f;
-    // pass 2: lanes of a warp take particles C apart in the block's order;
-    // particles of one cell sit next to each other (sampling order, kept by
-    // the binning), so neighbouring lanes come from different cells and their
-    // atomics hit different nodes instead of serialising on one address.
-    for (uint32_t qq = threadIdx.x; qq < (C << 5); qq += blockDim.x) {
-      const uint32_t i = (qq & 31u) * C + (qq >> 5);
-      if (i >= cnt) continue;
-      P2GPart q;
-      if (staged) {
-        q = P2GPart{sX[i], sA[i], sB[i], sC[i]};
-      } else {
-        const uint32_t p = v.perm[start + i];
-        q = P2GPart{v.cur.X[p], v.cur.VM0[p], v.cur.VM1[p], v.cur.VM2[p]};
+    for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
+      const uint32_t m = min(cnt - c0, CAP);
+#pragma unroll
+      for (uint32_t r = 0; r < C; ++r) {
+        const uint32_t i = lane + r * kP2GWarp;
+        if (i < m) {
+          const uint32_t p = v.perm[start + c0 + i];
+          cp_async16(&sX[i], &v.cur.X[p]);
+          cp_async16(&sA[i], &v.cur.VM0[p]);
+          cp_async16(&sB[i], &v.cur.VM1[p]);
+          cp_async16(&sC[i], &v.cur.VM2[p]);
+        }
       }
-      p2g_scatter<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
+      cp_async_wait_all();
+      __syncwarp();
+#pragma unroll 1
+      for (uint32_t r = 0; r < C; ++r) {
+        const uint32_t i = lane * C + r;
+        if (i < m) p2g_scatter<KIND>(s, v.mats, v.err, P2GPart{sX[i], sA[i], sB[i], sC[i]}, ox, oy, oz, Sm, Sp, sm);
+      }
+      __syncwarp();  // the next chunk overwrites the staged copies
     }
-    __syncthreads();
     const float iSm = 1.0f / Sm, iSp = 1.0f / Sp;
-    for (int j = threadIdx.x; j < NS; j += blockDim.x) {
+    for (int j = lane; j < NS; j += kP2GWarp) {
       int mi = sm[0][j];
       if (mi != 0) {
         int g, lx, ly, lz;
@@ -540,7 +513,13 @@ __global__ void __launch_bounds__(128) k_p2g(StepView v) {
                                              (float)sm[3][j] * iSp));
       }
     }
-    __syncthreads();
+    // the bounds are used: clear them for the step that next bins into this
+    // buffer (a probe reruns this P2G on the same particles and keeps them)
+    if (lane == 0 && !v.keep_gacc) {
+      v.bnd_cur[2 * key] = 0u;
+      v.bnd_cur[2 * key + 1] = 0u;
+    }
+    __syncwarp();  // the next block clears the accumulators
   }
 }
 
@@ -756,7 +735,9 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       v.nxt.ID[t] = id;
       if (v.nxt.E) v.nxt.E[t] = Ep;
       v.key_nxt[t] = nk;
-      warp_aggregated_inc(v.cnt_nxt, nk);
+      float bmass, bmom;
+      p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mn, bmass, bmom);
+      warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, nk, bmass, bmom);
     }
     __syncwarp();  // the next chunk (or block) overwrites the staged copies
     }
@@ -766,8 +747,10 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
 // Float64 pass of the precision extension: the particles G2P listed (F
 // degenerate, inverted or flagged by the scene's criteria) get the full
 // rotation-variant SVD and constitutive update in float64.  G2P stored the
-// advanced F' and M = m B'; this pass stores the projected F and subtracts
-// dt V0 tau from M.  Grid-stride over the list; an empty list returns at once.
+// advanced F' and M = m B'; this pass stores the projected F, subtracts
+// dt V0 tau from M and raises the particle's block bounds to cover the new M.
+// Grid-stride over the list; an empty list returns at once.
+template <int KIND>
 __global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
   const uint32_t n = (uint32_t)min(*v.fp64_count, (unsigned long long)v.n_cur);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -807,6 +790,12 @@ __global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
     v.nxt.F0[t] = make_float4(Ff[0], Ff[1], Ff[2], Ff[3]);
     v.nxt.F1[t] = make_float4(Ff[4], Ff[5], Ff[6], Ff[7]);
     v.nxt.F2[t] = Ff[8];
+    const float Mn[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    float bmass, bmom;
+    p2g_bounds<KIND>(s.inv_dx, mt.mass, a.x, a.y, a.z, Mn, bmass, bmom);
+    const uint32_t nk = v.key_nxt[t];
+    atomicMax(&v.bnd_nxt[2 * nk], __float_as_uint(bmass));
+    atomicMax(&v.bnd_nxt[2 * nk + 1], __float_as_uint(bmom));
   }
 }
 
@@ -992,9 +981,9 @@ __global__ void k_read_grid(const float4* Gacc, const float4* Gvel, const uint32
 // Append a new scene's particles: X (x, mat_base + mat), v, M = 0 (B = 0 and
 // tau(I) = 0), F = I, ID = index; plus keys and the histogram.
 template <int KIND>
-__global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene, uint32_t mat_base,
-                        uint32_t nmat, uint32_t start, uint32_t n, const float* x, const float* vel, const uint8_t* mat,
-                        const float* E, uint32_t* err) {
+__global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd, const SceneDev* scenes,
+                        const MatDev* mats, int scene, uint32_t mat_base, uint32_t nmat, uint32_t start, uint32_t n,
+                        const float* x, const float* vel, const uint8_t* mat, const float* E, uint32_t* err) {
   const SceneDev s = scenes[scene];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t t = start + i;
@@ -1027,7 +1016,10 @@ __global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* sc
     if (P.E) P.E[t] = E ? E[i] : 0.f;
     uint32_t k = particle_key<KIND>(s, ux, uy, uz);
     key[t] = k;
-    warp_aggregated_inc(cnt, k);
+    const float M0[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float bmass, bmom;
+    p2g_bounds<KIND>(s.inv_dx, mats[m].mass, vx, vy, vz, M0, bmass, bmom);
+    warp_aggregated_bin(cnt, bnd, k, bmass, bmom);
   }
 }
 
@@ -1035,8 +1027,8 @@ __global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* sc
 // upload of positions); particles already retired by a release keep the dead
 // key and leave the pool at the next step.
 template <int KIND>
-__global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, const MatDev* mats, uint32_t n,
-                        uint32_t* err) {
+__global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd, const SceneDev* scenes,
+                        const MatDev* mats, uint32_t n, uint32_t* err) {
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     if (key[t] == CK_DEAD_KEY) continue;  // retired by a release; its slot may already be reused
     float4 X = P.X[t];
@@ -1059,7 +1051,11 @@ __global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* sc
     }
     uint32_t k = particle_key<KIND>(s, ux, uy, uz);
     key[t] = k;
-    warp_aggregated_inc(cnt, k);
+    const float4 a = P.VM0[t], b = P.VM1[t], c = P.VM2[t];
+    const float M[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    float bmass, bmom;
+    p2g_bounds<KIND>(s.inv_dx, mt.mass, a.x, a.y, a.z, M, bmass, bmom);
+    warp_aggregated_bin(cnt, bnd, k, bmass, bmom);
   }
 }
 
@@ -1068,7 +1064,7 @@ __global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* sc
 template <int KIND>
 static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
-    case LK_P2G: k_p2g<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+    case LK_P2G: k_p2g<KIND><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v); break;
     case LK_UPDATE: k_grid_update<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
     case LK_G2P:
       // register budget of G2P: 16 warps/SM (128 registers) by default; 20
@@ -1081,7 +1077,7 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
       else
         k_g2p<KIND, 4><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
       break;
-    case LK_G2P_FP64: k_g2p_fp64<<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
+    case LK_G2P_FP64: k_g2p_fp64<KIND><<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
   }
 }
@@ -1121,27 +1117,30 @@ void launch_read_grid(int kind, cudaStream_t st, const StepView& v, int scene, i
                                           which, out);
 }
 
-void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes, int scene,
-                  uint32_t mat_base, uint32_t nmat, uint32_t start, uint32_t n, const float* x, const float* v,
-                  const uint8_t* mat, const float* E, uint32_t* err) {
+void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd,
+                  const SceneDev* scenes, const MatDev* mats, int scene, uint32_t mat_base, uint32_t nmat,
+                  uint32_t start, uint32_t n, const float* x, const float* v, const uint8_t* mat, const float* E,
+                  uint32_t* err) {
   int blocks = (int)((n + 255) / 256);
   if (blocks < 1) blocks = 1;
   if (blocks > 8192) blocks = 8192;
   if (kind == 0)
-    k_admit<0><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, scene, mat_base, nmat, start, n, x, v, mat, E, err);
+    k_admit<0><<<blocks, 256, 0, st>>>(P, key, cnt, bnd, scenes, mats, scene, mat_base, nmat, start, n, x, v, mat, E,
+                                        err);
   else
-    k_admit<1><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, scene, mat_base, nmat, start, n, x, v, mat, E, err);
+    k_admit<1><<<blocks, 256, 0, st>>>(P, key, cnt, bnd, scenes, mats, scene, mat_base, nmat, start, n, x, v, mat, E,
+                                        err);
 }
 
-void launch_rekey(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, const SceneDev* scenes,
-                  const MatDev* mats, uint32_t n, uint32_t* err) {
+void launch_rekey(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd,
+                  const SceneDev* scenes, const MatDev* mats, uint32_t n, uint32_t* err) {
   int blocks = (int)((n + 255) / 256);
   if (blocks < 1) blocks = 1;
   if (blocks > 8192) blocks = 8192;
   if (kind == 0)
-    k_rekey<0><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, mats, n, err);
+    k_rekey<0><<<blocks, 256, 0, st>>>(P, key, cnt, bnd, scenes, mats, n, err);
   else
-    k_rekey<1><<<blocks, 256, 0, st>>>(P, key, cnt, scenes, mats, n, err);
+    k_rekey<1><<<blocks, 256, 0, st>>>(P, key, cnt, bnd, scenes, mats, n, err);
 }
 
 }  // namespace ck

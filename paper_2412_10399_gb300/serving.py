@@ -20,7 +20,7 @@ from typing import Callable, Dict, List, Optional, Sequence
 
 # Device bytes per unit of each engine resource (see the layout in common.cuh):
 BYTES_PER_PARTICLE = 2 * (16 + 48 + 16 + 16 + 4 + 4) + 2 * 4 + 4 + 4  # two pools, keys x2, perm, float64 list
-BYTES_PER_KEY = 6 * 4                                              # histograms x2, offset, cursor, block list x2
+BYTES_PER_KEY = 6 * 4 + 2 * 2 * 4                                  # histograms x2, offset, cursor, block list x2, P2G bounds x2
 BYTES_PER_VIRTUAL_BLOCK = 2 * 4                                    # flag, table entry
 BYTES_PER_POOL_BLOCK_CK = 2 * 2 * 64 * 16 + 2 * 4                  # Gacc + Gvel for both grids, list entries
 

@@ -224,6 +224,26 @@ def _make_ctx(ck, scene, kernel, stream, timing=False):
     return ctx, keep
 
 
+def _kernel_breakdown(ck, scene, kernel, stream_ptr, warmup, steps):
+    """Average device ms per launch of each kernel over the same W + K steps,
+    from CUDA events recorded around every launch on the context's stream;
+    also the largest per-step count of float64-pass particles seen."""
+    ctx, keep = _make_ctx(ck, scene, kernel, stream_ptr)
+    ck.ckmpm_step(ctx, warmup)
+    ck.ckmpm_sync(ctx)
+    ck.ckmpm_set_timing(ctx, True)
+    ck.ckmpm_reset_timing(ctx)
+    fp64_max = 0
+    for _ in range(steps):
+        ck.ckmpm_step(ctx, 1)
+        if steps <= 400:
+            fp64_max = max(fp64_max, int(ck.ckmpm_get_stats(ctx).fp64_particles))
+    ck.ckmpm_sync(ctx)
+    st = ck.ckmpm_get_stats(ctx)
+    ck.ckmpm_destroy(ctx)
+    return {k: st.ms_kernel[i] for k, i in KERNEL_SLOT.items()}, fp64_max
+
+
 def _time_steps(ck, ctx, steps, stream_ptr):
     import torch
     stream = torch.cuda.ExternalStream(stream_ptr)
@@ -281,12 +301,12 @@ def run_gpu(args):
         scene.x, scene.v, scene.mat = scene.x[:k], scene.v[:k], scene.mat[:k]
     n = scene.n
 
-    # ---------------- device-resident timing of the CK path
+    # ---------------- device-resident timing of the CK path: W untimed steps,
+    # then K timed steps with no per-kernel events; the per-kernel breakdown
+    # comes from a second run over the same steps with events around each launch
     ctx, keep = _make_ctx(ck, scene, ck.KERNEL_CK, stream_ptr)
     ck.ckmpm_step(ctx, args.warmup)
     ck.ckmpm_sync(ctx)
-    ck.ckmpm_set_timing(ctx, True)
-    ck.ckmpm_reset_timing(ctx)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -296,15 +316,14 @@ def run_gpu(args):
     clocks = sampler.stop()
     ck.ckmpm_sync(ctx)
     st = ck.ckmpm_get_stats(ctx)
-    ck.ckmpm_set_timing(ctx, False)
     value, ms = aggregate_ranks(ms, n, args.steps, dist, device="cuda")
     if dist:
         dist.barrier()
-    per_kernel = {k: st.ms_kernel[i] for k, i in KERNEL_SLOT.items()}
     launches = int(st.launches_per_step) * args.steps
     fp64_frac = st.fp64_particles / max(1, n)
     n_pb, n_gb = int(st.n_particle_blocks), int(st.n_grid_blocks)
     ck.ckmpm_destroy(ctx)
+    per_kernel, fp64_max = _kernel_breakdown(ck, scene, ck.KERNEL_CK, stream_ptr, args.warmup, args.steps)
 
     dominant = max(("p2g", "g2p"), key=lambda k: per_kernel[k])
     peak, peak_src = _peaks()
@@ -317,20 +336,17 @@ def run_gpu(args):
                 "step_algorithmic_bytes_per_particle": sum(ALGO_BYTES.values()),
                 "step_frac": sum(ALGO_BYTES.values()) * n / (ms / args.steps / 1e3) / 1e9 / peak}
 
-    # ---------------- quadratic B-spline twin on the same inputs
-    qsteps = max(3, args.steps // 2)
+    # ---------------- quadratic B-spline twin on the same inputs and steps
+    qsteps = args.steps
     ctxq, keepq = _make_ctx(ck, scene, ck.KERNEL_QUADRATIC, stream_ptr)
-    ck.ckmpm_step(ctxq, max(1, args.warmup))
+    ck.ckmpm_step(ctxq, args.warmup)
     ck.ckmpm_sync(ctxq)
-    ck.ckmpm_set_timing(ctxq, True)
-    ck.ckmpm_reset_timing(ctxq)
     msq = _time_steps(ck, ctxq, qsteps, stream_ptr)
     ck.ckmpm_sync(ctxq)
-    stq = ck.ckmpm_get_stats(ctxq)
     ck.ckmpm_destroy(ctxq)
+    per_kernel_q, _ = _kernel_breakdown(ck, scene, ck.KERNEL_QUADRATIC, stream_ptr, args.warmup, qsteps)
     quad = {"value": n * qsteps / (msq / 1e3), "ms_per_step": msq / qsteps, "steps": qsteps,
-            "ck_speedup": (msq / qsteps) / (ms / args.steps),
-            "per_kernel_ms": {k: stq.ms_kernel[i] for k, i in KERNEL_SLOT.items()}}
+            "ck_speedup": (msq / qsteps) / (ms / args.steps), "per_kernel_ms": per_kernel_q}
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e_steps = max(2, min(args.steps, 10))
@@ -375,7 +391,10 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD, "particles_per_gpu": n, "particle_blocks": n_pb,
                            "grid_blocks": n_gb, "l2": "inputs larger than L2 (about 3.7 GB of particle state)",
                            "parallelism": "replicas" if world > 1 else "single",
-                           "fp64_svd_fraction": fp64_frac},
+                           "fp64_fraction_last_step": fp64_frac, "fp64_particles_max_step": fp64_max,
+                           "timed": f"steps {args.warmup}..{args.warmup + args.steps} of the scene (ball impact on "
+                                    f"the keep from about step 73)",
+                           "per_kernel_ms": "second run over the same steps with CUDA events around each launch"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "quadratic": quad, "served": served}
         print(json.dumps(line))
@@ -388,7 +407,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--max-particles", type=int, default=0,
                     help="keep only the first N particles of the scene (a slab of the castle base; "

@@ -55,6 +55,7 @@ struct MatDev {
   float mu, lam;  // Lame parameters
   float mass;     // rho * V0
   float alpha;    // Drucker-Prager cone coefficient
+  float dpc;      // Drucker-Prager: (3 lam + 2 mu) / (2 mu) alpha = alpha (1 + nu) / (1 - 2 nu), any E
   float E, nu;    // for per-particle E
 };
 

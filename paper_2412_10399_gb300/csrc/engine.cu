@@ -626,6 +626,7 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
     md.mass = (float)(m.rho * V0);
     double s = std::sin(m.friction_deg * M_PI / 180.0);
     md.alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s));
+    md.dpc = (float)((double)md.alpha * (1.0 + m.nu) / (1.0 - 2.0 * m.nu));
     md.E = (float)m.E;
     md.nu = (float)m.nu;
   }

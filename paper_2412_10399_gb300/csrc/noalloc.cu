@@ -199,6 +199,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
     hm[i].mass = (float)(m.rho * V0);
     double s = std::sin(m.friction_deg * M_PI / 180.0);
     hm[i].alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s));
+    hm[i].dpc = (float)((double)hm[i].alpha * (1.0 + m.nu) / (1.0 - 2.0 * m.nu));
     hm[i].E = (float)m.E;
     hm[i].nu = (float)m.nu;
     mmax = std::max(mmax, m.rho * V0);

@@ -377,6 +377,125 @@ __device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, 
   }
 }
 
+// ------------------------------------------- Drucker-Prager for small stretches
+//
+// Symmetric 3x3 matrices as (00, 11, 22, 01, 02, 12).  sym_mul forms A B for
+// commuting symmetric A and B (polynomials in one matrix), which is symmetric.
+__device__ __forceinline__ void sym_mul(const float* a, const float* b, float* c) {
+  c[0] = a[0] * b[0] + a[3] * b[3] + a[4] * b[4];
+  c[1] = a[3] * b[3] + a[1] * b[1] + a[5] * b[5];
+  c[2] = a[4] * b[4] + a[5] * b[5] + a[2] * b[2];
+  c[3] = a[0] * b[3] + a[3] * b[1] + a[4] * b[5];
+  c[4] = a[0] * b[4] + a[3] * b[5] + a[4] * b[2];
+  c[5] = a[3] * b[4] + a[1] * b[5] + a[5] * b[2];
+}
+
+// X = F F^T - I from D = F - I as D + D^T + D D^T (no cancellation against the
+// identity), and its largest row abs-sum.
+__device__ __forceinline__ float left_strain(const float* F, float* X) {
+  const float d[9] = {F[0] - 1.f, F[1], F[2], F[3], F[4] - 1.f, F[5], F[6], F[7], F[8] - 1.f};
+  X[0] = 2.f * d[0] + (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  X[1] = 2.f * d[4] + (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+  X[2] = 2.f * d[8] + (d[6] * d[6] + d[7] * d[7] + d[8] * d[8]);
+  X[3] = d[1] + d[3] + (d[0] * d[3] + d[1] * d[4] + d[2] * d[5]);
+  X[4] = d[2] + d[6] + (d[0] * d[6] + d[1] * d[7] + d[2] * d[8]);
+  X[5] = d[5] + d[7] + (d[3] * d[6] + d[4] * d[7] + d[5] * d[8]);
+  const float r0 = fabsf(X[0]) + fabsf(X[3]) + fabsf(X[4]);
+  const float r1 = fabsf(X[3]) + fabsf(X[1]) + fabsf(X[5]);
+  const float r2 = fabsf(X[4]) + fabsf(X[5]) + fabsf(X[2]);
+  return fmaxf(r0, fmaxf(r1, r2));
+}
+
+// The Drucker-Prager update of Sec. 3.2 step 4 (klar2016 return map, Hencky
+// elasticity) without an eigen-decomposition, for F F^T = I + X with the
+// largest row abs-sum of X at most 1/32 (every stretch within about 1.6% of 1).
+// The log strain is a matrix function of the left stretch V = (F F^T)^(1/2):
+// L = log V = log(I + X) / 2 has the eigenvectors U of F F^T and eigenvalues
+// eps_i = ln sigma_i, so tr eps = tr L and |eps^| = |dev L|_F.  The return map
+// moves eps along eps^ (or to 0 at the tip), which is L_new = L - k dev L (or
+// 0); then F_new = U diag(exp(eps_new - eps)) U^T F = exp(L_new - L) F and the
+// Hencky stress is 2 mu L_new + lam tr(L_new) I.  log(I + X) is its series
+// through X^5 (truncation below |X|^6 / 6 < 1.2e-9 |X|), exp(Y) its series
+// through Y^4 (|Y| <= 2 |L| <= 1/32: truncation below 2.6e-10 |Y|), both in
+// Horner form with products of commuting symmetric matrices.
+__device__ __forceinline__ void dp_small_strain(float* F, const float* X, float mu, float lam, float dpc,
+                                                float* tau) {
+  float Z[6], W[6];
+  // log(I + X) = X (I - X (1/2 I - X (1/3 I - X (1/4 I - X / 5))))
+#pragma unroll
+  for (int q = 0; q < 6; ++q) Z[q] = -0.2f * X[q] + (q < 3 ? 0.25f : 0.f);
+  const float c[3] = {1.f / 3.f, 0.5f, 1.f};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sym_mul(X, Z, W);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Z[q] = -W[q] + (q < 3 ? c[k] : 0.f);
+  }
+  float L[6];
+  sym_mul(X, Z, L);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) L[q] *= 0.5f;
+  const float tr = L[0] + L[1] + L[2];
+  const float h[6] = {L[0] - tr * (1.f / 3.f), L[1] - tr * (1.f / 3.f), L[2] - tr * (1.f / 3.f), L[3], L[4], L[5]};
+  const float nrm = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2] + 2.f * (h[3] * h[3] + h[4] * h[4] + h[5] * h[5]));
+  float Ln[6] = {L[0], L[1], L[2], L[3], L[4], L[5]};
+  float Y[6];
+  bool moved = false;
+  if (tr >= 0.f || nrm <= 0.f) {  // tension or purely volumetric: the tip
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      Ln[q] = 0.f;
+      Y[q] = -L[q];
+    }
+    moved = true;
+  } else {
+    const float dg = nrm + dpc * tr;
+    if (dg > 0.f) {
+      const float k = dg / nrm;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        Y[q] = -k * h[q];
+        Ln[q] = L[q] + Y[q];
+      }
+      moved = true;
+    }
+  }
+  if (moved) {
+    // exp(Y) = I + Y (I + Y (1/2 I + Y (1/6 I + Y / 24)))
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Z[q] = Y[q] * (1.f / 24.f) + (q < 3 ? 1.f / 6.f : 0.f);
+    const float e[2] = {0.5f, 1.f};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      sym_mul(Y, Z, W);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Z[q] = W[q] + (q < 3 ? e[k] : 0.f);
+    }
+    float Ex[6];
+    sym_mul(Y, Z, Ex);
+    Ex[0] += 1.f;
+    Ex[1] += 1.f;
+    Ex[2] += 1.f;
+    const float Em[9] = {Ex[0], Ex[3], Ex[4], Ex[3], Ex[1], Ex[5], Ex[4], Ex[5], Ex[2]};
+    float Fn[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        CK_M(Fn, i, j) = CK_M(Em, i, 0) * CK_M(F, 0, j) + CK_M(Em, i, 1) * CK_M(F, 1, j) + CK_M(Em, i, 2) * CK_M(F, 2, j);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) F[q] = Fn[q];
+  }
+  const float trn = Ln[0] + Ln[1] + Ln[2];
+  const float m2 = 2.f * mu, vol = lam * trn;
+  tau[0] = m2 * Ln[0] + vol;
+  tau[4] = m2 * Ln[1] + vol;
+  tau[8] = m2 * Ln[2] + vol;
+  tau[1] = tau[3] = m2 * Ln[3];
+  tau[2] = tau[6] = m2 * Ln[4];
+  tau[5] = tau[7] = m2 * Ln[5];
+}
+
 // Kirchhoff stress of a given F without plasticity (used by readback/upload).
 template <typename T>
 __device__ __forceinline__ void stress_only(int model, const T* F, T mu, T lam, T* tau) {

@@ -668,7 +668,14 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       // inverted F is deferred to the float64 pass (precision extension):
       // this kernel stores F' and M = m B' (no stress) and lists the particle
       float tau[9];
-      {
+      // Drucker-Prager at small stretch: matrix log/exp series, no eigen-
+      // decomposition (such F is far from every float64 criterion)
+      float Xs[6];
+      const bool small_dp = mt.model == 1 && s.gap_tol <= 0.f && s.j_tol < 0.9f && s.cond_tol < 0.9f &&
+                            left_strain(F, Xs) <= 0.03125f;
+      if (small_dp) {
+        dp_small_strain(F, Xs, mu, lam, mt.dpc, tau);
+      } else {
         // b = F F^T = U diag(sigma^2) U^T
         float bq[9], U[9], e[3], sg[3];
 #pragma unroll

@@ -85,10 +85,14 @@ def test_p2g_grid_parity_dense_blocks(kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("model", MODELS)
-def test_one_step_particle_parity(kernel, model):
+@pytest.mark.parametrize("model,f_scale", [(S.FIXED_COROTATED, 0.08), (S.DRUCKER_PRAGER, 0.08),
+                                           (S.DRUCKER_PRAGER, 0.008)])
+def test_one_step_particle_parity(kernel, model, f_scale):
+    """f_scale 0.008 keeps F F^T within 1/32 of I for nearly every particle, so
+    Drucker-Prager takes the small-stretch matrix-series update (elastic,
+    plastic and tip cases all occur); 0.08 takes the eigen-decomposition."""
     ck = need_gpu()
-    sc, B, F = random_scene(5000, 32, 7, model=model, kernel=kernel, f_scale=0.08)
+    sc, B, F = random_scene(5000, 32, 7, model=model, kernel=kernel, f_scale=f_scale)
     sim = _sim(ck, sc, B, F)
     sim.step(1)
     sim.sync()

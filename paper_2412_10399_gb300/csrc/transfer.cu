@@ -140,7 +140,7 @@ struct Sten<0> {
   int r[2][3];        // base node of each slot relative to the block origin
   float w[2][3][2];   // per slot, axis, node
   float d[2][3][2];
-  float Di[9];
+  float li[3], y[3], den;  // D^-1 = diag(li) - den y y^T (cells^-2)
   __device__ __forceinline__ bool set(float ux, float uy, float uz, int ox, int oy, int oz) {
     float u[3] = {ux, uy, uz};
     int o[3] = {ox, oy, oz};
@@ -168,13 +168,12 @@ struct Sten<0> {
       s[a] = sg;
     }
     // Lambda_a in [0.0826, 0.1586] and 1 + s^T Lambda^-1 s in [1, 1.3]
-    float li[3] = {rcp_nr(lam[0]), rcp_nr(lam[1]), rcp_nr(lam[2])};
-    float y[3] = {li[0] * s[0], li[1] * s[1], li[2] * s[2]};
-    float den = rcp_nr(1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Di[i * 3 + j] = (i == j ? li[i] : 0.0f) - y[i] * y[j] * den;
+    for (int a = 0; a < 3; ++a) {
+      li[a] = rcp_nr(lam[a]);
+      y[a] = li[a] * s[a];
+    }
+    den = rcp_nr(1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
     return ok;
   }
 };
@@ -328,17 +327,20 @@ __device__ __forceinline__ void g2p_gather(const Sten<1>& st, const float4* sv, 
   }
 }
 
-template <int KIND>
-__device__ __forceinline__ void dinv_of(const Sten<KIND>& st, float* Di);
-template <>
-__device__ __forceinline__ void dinv_of(const Sten<0>& st, float* Di) {
+// R = scale Q D^-1 for a row-major 3x3 Q.  CK: D^-1 = diag(li) - den y y^T,
+// so each row costs one dot product with y and three fused updates instead of
+// a full 3x3 product; quadratic: D^-1 = 4 I.
+__device__ __forceinline__ void mul_dinv(const Sten<0>& st, const float* Q, float scale, float* R) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) Di[i] = st.Di[i];
+  for (int r = 0; r < 3; ++r) {
+    const float t = (Q[r * 3] * st.y[0] + Q[r * 3 + 1] * st.y[1] + Q[r * 3 + 2] * st.y[2]) * st.den;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) R[r * 3 + q] = scale * (Q[r * 3 + q] * st.li[q] - t * st.y[q]);
+  }
 }
-template <>
-__device__ __forceinline__ void dinv_of(const Sten<1>& st, float* Di) {
+__device__ __forceinline__ void mul_dinv(const Sten<1>&, const float* Q, float scale, float* R) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) Di[i] = (i % 4 == 0) ? 4.0f : 0.0f;
+  for (int q = 0; q < 9; ++q) R[q] = (4.0f * scale) * Q[q];
 }
 
 __device__ __forceinline__ void decode_block(const SceneDev& s, uint32_t key, int& ox, int& oy, int& oz) {
@@ -426,17 +428,10 @@ __device__ __forceinline__ void p2g_scatter(const SceneDev& s, const MatDev* mat
     flag_error(err, CK_ERR_INTERNAL);
     return;
   }
-  float Di[9];
-  dinv_of<KIND>(st, Di);
   const float M[9] = {q.a.w, q.b.x, q.b.y, q.b.z, q.b.w, q.c.x, q.c.y, q.c.z, q.c.w};
   // A^ = M D^-1 / dx so that A (x_i - x_p) = A^ (offset in cells), pre-scaled
   float A[9];
-  const float ks = s.inv_dx * Sp;
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      A[r * 3 + k] = (M[r * 3 + 0] * Di[0 * 3 + k] + M[r * 3 + 1] * Di[1 * 3 + k] + M[r * 3 + 2] * Di[2 * 3 + k]) * ks;
+  mul_dinv(st, M, s.inv_dx * Sp, A);
   const float mass = mats[__float_as_uint(q.X.w)].mass;
   const float ms = mass * Sm;
   const float px = mass * q.a.x * Sp, py = mass * q.a.y * Sp, pz = mass * q.a.z * Sp;
@@ -646,17 +641,12 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       float vel[3], Bh[9];
       g2p_gather(st, sv, vel, Bh);
       const float vx = vel[0], vy = vel[1], vz = vel[2];
-      float Di[9];
-      dinv_of<KIND>(st, Di);
-      // C = B D^-1 = Bh Di / dx ; F' = (I + dt C) F
+      // C = B D^-1 = Bh D^-1 / dx ; F' = (I + dt C) F
       float G[9];
-      const float k = s.dt * s.inv_dx;
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          G[r * 3 + q] = (r == q ? 1.0f : 0.0f) +
-                         k * (Bh[r * 3 + 0] * Di[0 * 3 + q] + Bh[r * 3 + 1] * Di[1 * 3 + q] + Bh[r * 3 + 2] * Di[2 * 3 + q]);
+      mul_dinv(st, Bh, s.dt * s.inv_dx, G);
+      G[0] += 1.0f;
+      G[4] += 1.0f;
+      G[8] += 1.0f;
       const float Fo[9] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2};
       float F[9];
 #pragma unroll
@@ -714,7 +704,8 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
       // next key; particles leaving the interior are clamped and flagged
       float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
-      bool fin = isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(vx) && isfinite(vy) && isfinite(vz);
+      // x was finite, so x + dt v is finite when v is
+      bool fin = isfinite(vx) && isfinite(vy) && isfinite(vz);
 #pragma unroll
       for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]);
       if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
@@ -894,12 +885,9 @@ __global__ void k_read_particles(Pool P, const SceneDev* scenes, const MatDev* m
         Cell<KIND> cx, cy, cz;
         cx.set(ux); cy.set(uy); cz.set(uz);
         st.set(ux, uy, uz, cx.block() * 4, cy.block() * 4, cz.block() * 4);
-        float Di[9];
-        dinv_of<KIND>(st, Di);
-        float k = s.inv_dx * s.inv_dx;
-        for (int r = 0; r < 3; ++r)
-          for (int q = 0; q < 3; ++q)
-            out[9 * id + r * 3 + q] = k * (B[r * 3] * Di[q] + B[r * 3 + 1] * Di[3 + q] + B[r * 3 + 2] * Di[6 + q]);
+        float C[9];
+        mul_dinv(st, B, s.inv_dx * s.inv_dx, C);
+        for (int q = 0; q < 9; ++q) out[9 * id + q] = C[q];
       }
     }
   }

@@ -4,10 +4,11 @@
 // / re-keying).  One step then runs:
 //   scan_tiles  per 4096-key tile: particle count and non-empty key count
 //   scan_top    one CTA: exclusive scan over tiles; resets per-step counters
-//   scan_final  per key: offset and scatter cursor; non-empty keys become the
-//               particle-block list (in key order, so the list is
-//               deterministic) and flag the 2x2x2 grid blocks they touch;
-//               the next histogram is cleared
+//   scan_final  per non-empty key: offset and scatter cursor; non-empty keys
+//               become the particle-block list (in key order, so the list is
+//               deterministic) and flag the 2x2x2 grid blocks they touch
+// (G2P clears each histogram entry it has used, so the buffer it fills next
+// step starts at zero without a pass over the whole key space.)
 //   scatter     perm[cursor[key]++] = particle (warp-aggregated atomics)
 //   glist       flagged grid blocks -> active grid-block list; flags cleared
 #include <cuda_runtime.h>
@@ -133,10 +134,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
   const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kPerThread;
   uint32_t c[kPerThread];
   uint32_t tc = 0, tn = 0;
+  if (base + kPerThread <= v.n_keys) {  // 16 consecutive counts as four 16-byte loads
+    const uint4* p4 = reinterpret_cast<const uint4*>(v.cnt_cur + base);
+#pragma unroll
+    for (int q = 0; q < kPerThread / 4; ++q) {
+      const uint4 x = p4[q];
+      c[4 * q] = x.x;
+      c[4 * q + 1] = x.y;
+      c[4 * q + 2] = x.z;
+      c[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q) c[q] = base + q < v.n_keys ? v.cnt_cur[base + q] : 0u;
+  }
 #pragma unroll
   for (int q = 0; q < kPerThread; ++q) {
-    uint32_t k = base + q;
-    c[q] = k < v.n_keys ? v.cnt_cur[k] : 0u;
     tc += c[q];
     tn += c[q] ? 1u : 0u;
   }
@@ -168,10 +181,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
   for (int q = 0; q < kPerThread; ++q) {
     uint32_t k = base + q;
     if (k >= v.n_keys) break;
-    v.offset[k] = pc;
-    v.cursor[k] = pc;
-    v.cnt_nxt[k] = 0u;
     if (c[q]) {
+      v.offset[k] = pc;
+      v.cursor[k] = pc;
       int sl = scene_of_key(bs, k);
       v.pb_key[pn] = k;
       v.pb_scene[pn] = (uint32_t)sl;

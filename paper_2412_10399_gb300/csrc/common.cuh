@@ -78,7 +78,7 @@ struct StepView {
   uint32_t* key_cur;    // keys of cur (input of the sort)
   uint32_t* key_nxt;    // keys written by G2P for nxt
   uint32_t* cnt_cur;    // histogram of key_cur over the key space
-  uint32_t* cnt_nxt;    // histogram written by G2P
+  uint32_t* cnt_nxt;    // histogram written by G2P (all zero before it: G2P clears cnt_cur after use)
   uint32_t* bnd_cur;    // per key: P2G contribution bounds (mass, momentum) of cur, float
                         // bits; P2G clears an active block's pair after use
   uint32_t* bnd_nxt;    // the same for nxt, written by G2P (all zero before it)

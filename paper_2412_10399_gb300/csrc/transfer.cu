@@ -739,6 +739,9 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
     }
     __syncwarp();  // the next chunk (or block) overwrites the staged copies
     }
+    // last use of the block's count this step: clear it, so that this buffer
+    // is all zero when G2P fills it as the next histogram
+    if (threadIdx.x == 0) v.cnt_cur[key] = 0u;
   }
 }
 

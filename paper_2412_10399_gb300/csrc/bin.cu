@@ -200,12 +200,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
   }
 }
 
-__global__ void k_scatter(StepView v) {
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n_cur; j += gridDim.x * blockDim.x) {
-    uint32_t key = v.key_cur[j];
-    if (key == CK_DEAD_KEY) continue;
-    uint32_t pos = warp_aggregated_inc(v.cursor, key);
-    v.perm[pos] = j;
+// Each warp handles kScatterUnroll groups of 32 particles per pass and issues
+// the cursor atomics of all of them before it waits for the first result: the
+// pass is one atomic round trip instead of kScatterUnroll.
+constexpr int kScatterUnroll = 4;
+
+__global__ void __launch_bounds__(256) k_scatter(StepView v) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t stride = gridDim.x * blockDim.x * kScatterUnroll;
+  // the loop runs on the warp's first index, so every lane of a warp takes
+  // the same iterations (the full-mask warp intrinsics below need that)
+  for (uint32_t w0 = blockIdx.x * blockDim.x * kScatterUnroll + (threadIdx.x - lane) * kScatterUnroll;
+       w0 < v.n_cur; w0 += stride) {
+    const uint32_t j0 = w0 + lane;
+    uint32_t key[kScatterUnroll], peers[kScatterUnroll], base[kScatterUnroll];
+#pragma unroll
+    for (int u = 0; u < kScatterUnroll; ++u) {
+      const uint32_t j = j0 + 32u * u;
+      key[u] = j < v.n_cur ? v.key_cur[j] : CK_DEAD_KEY;
+    }
+#pragma unroll
+    for (int u = 0; u < kScatterUnroll; ++u) {
+      peers[u] = __match_any_sync(0xffffffffu, key[u]);
+      base[u] = 0u;
+      if (key[u] != CK_DEAD_KEY && (int)lane == __ffs(peers[u]) - 1)
+        base[u] = atomicAdd(&v.cursor[key[u]], (uint32_t)__popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < kScatterUnroll; ++u) {
+      const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
+      if (key[u] != CK_DEAD_KEY) v.perm[b + __popc(peers[u] & ((1u << lane) - 1u))] = j0 + 32u * u;
+    }
   }
 }
 

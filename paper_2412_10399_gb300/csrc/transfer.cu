@@ -1063,7 +1063,9 @@ template <int KIND>
 static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
     case LK_P2G: k_p2g<KIND><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v); break;
-    case LK_UPDATE: k_grid_update<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
+    // a wide grid: each CTA's block loop is short, so the dependent loads of
+    // one block (list entry, scene, accumulators) overlap across CTAs
+    case LK_UPDATE: k_grid_update<KIND><<<lc.sm_count * 64, 128, 0, lc.stream>>>(v); break;
     case LK_G2P:
       // register budget of G2P: 16 warps/SM (128 registers) by default; 20
       // or 24 (96 / 80 registers, no spills either) on request: measured

@@ -198,6 +198,43 @@ def test_fp64_svd_path_is_taken_and_matches():
     assert rel(vg, new.v.numpy()) <= 1e-4
 
 
+@pytest.mark.parametrize("model", MODELS)
+def test_fp64_pass_mixed_blocks_two_steps(model):
+    """Every other particle has a nearly singular F (J ~ 1e-3 < j_tol), so the
+    default criteria send it to the float64 pass while its neighbours in the
+    same blocks stay in float32.  The pass rewrites M after G2P recorded the
+    block bounds, so the next P2G (checked on the grids) relies on the pass
+    raising them; two steps are then compared with the oracle."""
+    ck = need_gpu()
+    sc, B, F = random_scene(3000, 16, 13, model=model, f_scale=0.02)
+    F = F.astype(np.float64)
+    F[::2, :, 2] *= 1e-3
+    F = f32(F)
+    sim = _sim(ck, sc, B, F)
+    sim.step(1)
+    sim.sync()
+    n64 = int(sim.stats().fp64_particles)
+    sim.probe_grids()
+    gm = sim.read(ck.FIELD_GRID_M)
+    gp = sim.read(ck.FIELD_GRID_P)
+    sim.step(1)
+    sim.sync()
+    Fg = sim.read(ck.FIELD_F)
+    vg = sim.read(ck.FIELD_V)
+    sim.close()
+    assert n64 >= sc.n // 2 - 5 and n64 <= sc.n // 2 + 5
+    prm = O.params_from_scene(sc)
+    st1 = O.step(oracle_state(sc, B, F), prm)
+    grids = O.p2g(st1, prm)
+    nn = sc.res + 1
+    for gi, k in enumerate(O.grid_ids(sc.kernel)):
+        assert rel(gm[gi], grids[k][0].numpy().reshape(nn, nn, nn)) <= 1e-5
+        assert rel(gp[gi], grids[k][1].numpy().reshape(nn, nn, nn, 3)) <= 1e-5
+    st2 = O.step(st1, prm)
+    assert rel(Fg, st2.F.numpy()) <= 5e-6
+    assert rel(vg, st2.v.numpy()) <= 2e-4
+
+
 def test_upload_readback_roundtrip():
     ck = need_gpu()
     sc, B, F = random_scene(3000, 16, 11, f_scale=0.1)

@@ -409,6 +409,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   if (const char* e = getenv("CKMPM_CTAS_PER_SM")) per_sm = std::max(1, atoi(e));
   ctx->lc.persistent_ctas = ctx->sm_count * per_sm;
   ctx->lc.sm_count = ctx->sm_count;
+  ctx->lc.g2p_minb = cfg->kernel == 0 ? 5 : 4;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;

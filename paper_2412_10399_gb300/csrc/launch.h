@@ -12,7 +12,7 @@ struct LaunchCfg {
   cudaStream_t stream;
   int persistent_ctas;  // CTAs of the persistent P2G / update / G2P launches
   int sm_count = 1;     // SMs of the device (grid of the float64 pass)
-  int g2p_minb = 4;     // resident G2P CTAs per SM the register budget targets
+  int g2p_minb = 4;     // resident G2P warps per SM / 4 the register budget targets
 };
 
 enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4 };

@@ -561,14 +561,16 @@ __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(
 // G2P runs one warp per CTA: a particle block's ~400-500 particles leave a
 // partly idle last round on 32 lanes instead of on 128, and the staging
 // waits are warp-level, so a lane that finishes early never holds up three
-// other warps at a block barrier.  MINB counts 4-warp equivalents per SM.
+// other warps at a block barrier.  MINB counts 4-warp equivalents per SM; at
+// 5 or more the staging chunk shrinks to 64 particles so that shared memory
+// admits the extra warps.
 constexpr int kG2PWarp = 32;
-constexpr int kG2PStage = 128;  // particles staged per chunk
+__host__ __device__ constexpr int g2p_stage(int minb) { return minb >= 5 ? 64 : 128; }  // particles per chunk
 
 template <int KIND, int MINB>
 __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  constexpr int CAP = kG2PStage;
+  constexpr int CAP = g2p_stage(MINB);
   __shared__ float4 sv[NS];  // staged v~ (w unused): one 16-byte shared load per node
   __shared__ float4 sX[CAP], sF0[CAP], sF1[CAP];
   __shared__ float sF2[CAP], sE[CAP];
@@ -1067,9 +1069,10 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
     // one block (list entry, scene, accumulators) overlap across CTAs
     case LK_UPDATE: k_grid_update<KIND><<<lc.sm_count * 64, 128, 0, lc.stream>>>(v); break;
     case LK_G2P:
-      // register budget of G2P: 16 warps/SM (128 registers) by default; 20
-      // or 24 (96 / 80 registers, no spills either) on request: measured
-      // slower.  One resident wave of one-warp CTAs.
+      // register budget of G2P: 20 warps/SM (96 registers, 64-particle
+      // chunks) for the compact kernel and 16 (128 registers) for the
+      // quadratic twin by default, the faster of each on the large-impact
+      // scene; 24 (80 registers) on request.  One resident wave.
       if (lc.g2p_minb >= 6)
         k_g2p<KIND, 6><<<lc.sm_count * 24, kG2PWarp, 0, lc.stream>>>(v);
       else if (lc.g2p_minb == 5)

@@ -408,25 +408,25 @@ __device__ __forceinline__ float left_strain(const float* F, float* X) {
 
 // The Drucker-Prager update of Sec. 3.2 step 4 (klar2016 return map, Hencky
 // elasticity) without an eigen-decomposition, for F F^T = I + X with the
-// largest row abs-sum of X at most 1/32 (every stretch within about 1.6% of 1).
+// largest row abs-sum of X at most 1/48 (every stretch within about 1% of 1).
 // The log strain is a matrix function of the left stretch V = (F F^T)^(1/2):
 // L = log V = log(I + X) / 2 has the eigenvectors U of F F^T and eigenvalues
 // eps_i = ln sigma_i, so tr eps = tr L and |eps^| = |dev L|_F.  The return map
 // moves eps along eps^ (or to 0 at the tip), which is L_new = L - k dev L (or
 // 0); then F_new = U diag(exp(eps_new - eps)) U^T F = exp(L_new - L) F and the
 // Hencky stress is 2 mu L_new + lam tr(L_new) I.  log(I + X) is its series
-// through X^5 (truncation below |X|^6 / 6 < 1.2e-9 |X|), exp(Y) its series
-// through Y^4 (|Y| <= 2 |L| <= 1/32: truncation below 2.6e-10 |Y|), both in
+// through X^4 (truncation below |X|^5 / 5 < 4e-8 |X|), exp(Y) its series
+// through Y^4 (|Y| <= 2 |L| <= 1/48: truncation below 5e-11 |Y|), both in
 // Horner form with products of commuting symmetric matrices.
 __device__ __forceinline__ void dp_small_strain(float* F, const float* X, float mu, float lam, float dpc,
                                                 float* tau) {
   float Z[6], W[6];
-  // log(I + X) = X (I - X (1/2 I - X (1/3 I - X (1/4 I - X / 5))))
+  // log(I + X) = X (I - X (1/2 I - X (1/3 I - X / 4)))
 #pragma unroll
-  for (int q = 0; q < 6; ++q) Z[q] = -0.2f * X[q] + (q < 3 ? 0.25f : 0.f);
-  const float c[3] = {1.f / 3.f, 0.5f, 1.f};
+  for (int q = 0; q < 6; ++q) Z[q] = -0.25f * X[q] + (q < 3 ? 1.f / 3.f : 0.f);
+  const float c[2] = {0.5f, 1.f};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 2; ++k) {
     sym_mul(X, Z, W);
 #pragma unroll
     for (int q = 0; q < 6; ++q) Z[q] = -W[q] + (q < 3 ? c[k] : 0.f);

@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       // decomposition (such F is far from every float64 criterion)
       float Xs[6];
       const bool small_dp = mt.model == 1 && s.gap_tol <= 0.f && s.j_tol < 0.9f && s.cond_tol < 0.9f &&
-                            left_strain(F, Xs) <= 0.03125f;
+                            left_strain(F, Xs) <= (1.f / 48.f);
       if (small_dp) {
         dp_small_strain(F, Xs, mu, lam, mt.dpc, tau);
       } else {

@@ -152,7 +152,7 @@ struct Sten<0> {
       c.set(u[a]);
       r[0][a] = c.bm - o[a];
       r[1][a] = c.bp - o[a];
-      ok = ok && (r[0][a] >= 0) && (r[0][a] <= 3) && (r[1][a] >= 0) && (r[1][a] <= 4);
+      ok = ok && (unsigned)r[0][a] <= 3u;  // then the G+ base, r[0][a] or r[0][a] + 1, is in [0, 4]
       float sg = sin_2pi(c.fp) * kInv2Pi;
       w[1][a][0] = 1.0f - c.fp + sg;
       w[1][a][1] = c.fp - sg;
@@ -192,7 +192,7 @@ struct Sten<1> {
       Cell<1> c;
       c.set(u[a]);
       r[a] = c.b - o[a];
-      ok = ok && (r[a] >= 0) && (r[a] <= 3);
+      ok = ok && (unsigned)r[a] <= 3u;
       float f = c.f;
       w[a][0] = 0.5f * (1.5f - f) * (1.5f - f);
       w[a][1] = 0.75f - (f - 1.0f) * (f - 1.0f);

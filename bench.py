@@ -180,6 +180,19 @@ def _cpu_sample():
     return sc
 
 
+def _cpu_model():
+    """CPU model string of the host (from /proc/cpuinfo where present)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu part", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(steps: int = 2):
     import torch
     from oracle import ckmpm_oracle as O
@@ -191,6 +204,7 @@ def cpu_baseline(steps: int = 2):
         st = O.step(st, prm)
     dt = time.perf_counter() - t0
     return {"value": sc.n * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "host": f"{os.cpu_count()} logical CPUs, {_cpu_model()}",
             "sample": f"{sc.n} particles (castle-base window of the 16.27M scene, same dx/dt/material), "
                       f"{steps} FP64 steps, {dt:.1f} s"}
 
@@ -331,6 +345,7 @@ def run_gpu(args):
     traffic = _traffic(dominant)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
+                "frac_of_nominal_7900_gbs": achieved / 7900.0,
                 "algorithmic_bytes_per_particle": ALGO_BYTES[dominant], "traffic": traffic,
                 "per_kernel_ms": per_kernel,
                 "step_algorithmic_bytes_per_particle": sum(ALGO_BYTES.values()),

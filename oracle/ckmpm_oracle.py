@@ -36,6 +36,12 @@ Readings where the paper is silent or garbled (each one is a named choice):
      hardening), alpha = sqrt(2/3) * 2 sin(phi) / (3 - sin(phi)).
   R10 step order: tau(F^n) -> P2G -> grid update -> G2P -> F -> return map
      -> x^{n+1}.
+  R15 J-based fluid (the dam-break scenes of the performance section, an
+     equation of state after monaghan1994 / tampubolon2017, both only cited):
+     pressure p = B (J^-gamma - 1), Kirchhoff stress tau = -J p I, and the
+     particle keeps only its volume ratio, F <- J^(1/3) I after each F update
+     (the shear part of F carries no stress in a fluid).  The paper lists a
+     viscosity 0.1 without its discretisation; it is not modelled.
   Quadratic comparison path: hu2018 MLS-MPM on one grid with the quadratic
   B-spline, D = dx^2/4 I.
 """
@@ -52,6 +58,7 @@ TWO_PI = 2.0 * math.pi
 
 FIXED_COROTATED = 0
 DRUCKER_PRAGER = 1
+J_FLUID = 2
 KERNEL_CK = 0
 KERNEL_QUADRATIC = 1
 
@@ -114,10 +121,11 @@ def stencil(x: torch.Tensor, dx: float, kernel: int, k: int):
 @dataclasses.dataclass
 class Mat:
     model: int
-    E: float
+    E: float            # Young's modulus; for the fluid, the equation-of-state constant B
     nu: float
     rho: float
     friction_deg: float = 0.0
+    gamma: float = 7.15  # fluid equation-of-state exponent
 
 
 @dataclasses.dataclass
@@ -291,6 +299,24 @@ def dp_return_map(F, mu, lam, alpha):
     return torch.where(unchanged[..., None], F, Fn)
 
 
+def fluid_pressure(J, Bk, gamma):
+    """Reading R15: equation of state p = B (J^-gamma - 1)."""
+    return Bk * (J ** (-gamma) - 1.0)
+
+
+def fluid_kirchhoff(F, Bk, gamma):
+    """Reading R15: tau = J sigma = -J p I for the J-based fluid, J = det F."""
+    J = torch.det(F)
+    I = torch.eye(3, dtype=F.dtype).expand_as(F)
+    return (-J * fluid_pressure(J, Bk, gamma))[..., None, None] * I
+
+
+def fluid_energy(J, Bk, gamma):
+    """Stored energy per reference volume whose Kirchhoff stress is R15's:
+    tau = J psi'(J) I with psi'(J) = -p(J), psi(1) = 0."""
+    return -Bk * ((J ** (1.0 - gamma) - 1.0) / (1.0 - gamma) - (J - 1.0))
+
+
 def kirchhoff_stress(st: State, prm: Params, newton=False) -> torch.Tensor:
     mu, lam = particle_lame(st, prm)
     models = torch.tensor([m.model for m in prm.materials])[st.mat]
@@ -303,12 +329,23 @@ def kirchhoff_stress(st: State, prm: Params, newton=False) -> torch.Tensor:
     if dp.any():
         tau_dp = hencky_kirchhoff(st.F, mu, lam)
         tau = torch.where(dp[:, None, None], tau_dp, tau)
+    fl = models == J_FLUID
+    if fl.any():
+        Bk = torch.tensor([m.E for m in prm.materials], dtype=F64)[st.mat]
+        gam = torch.tensor([m.gamma for m in prm.materials], dtype=F64)[st.mat]
+        tau = torch.where(fl[:, None, None], fluid_kirchhoff(st.F, Bk, gam), tau)
     return tau
 
 
 def plasticity(F: torch.Tensor, st: State, prm: Params) -> torch.Tensor:
-    """Return mapping (Sec. 3.2 step 4) for plastic materials; identity otherwise."""
+    """Return mapping (Sec. 3.2 step 4) for plastic materials, the volumetric
+    projection F <- J^(1/3) I for the fluid (reading R15); identity otherwise."""
     models = torch.tensor([m.model for m in prm.materials])[st.mat]
+    fl = models == J_FLUID
+    if fl.any():
+        J = torch.det(F)
+        c = torch.sign(J) * torch.abs(J) ** (1.0 / 3.0)
+        F = torch.where(fl[:, None, None], c[:, None, None] * torch.eye(3, dtype=F64), F)
     dp = models == DRUCKER_PRAGER
     if not dp.any():
         return F
@@ -469,7 +506,7 @@ def grid_angular_momentum(grids, prm: Params):
 
 def params_from_scene(sc) -> Params:
     """Build oracle parameters from a scene description (duck-typed)."""
-    mats = [Mat(m.model, m.E, m.nu, m.rho, m.friction_deg) for m in sc.materials]
+    mats = [Mat(m.model, m.E, m.nu, m.rho, m.friction_deg, getattr(m, "gamma", 7.15)) for m in sc.materials]
     return Params(res=sc.res, dx=sc.dx, dt=sc.dt, materials=mats, gravity=tuple(sc.gravity),
                   bc_cells=sc.bc_cells, ppc=sc.ppc, kernel=sc.kernel)
 

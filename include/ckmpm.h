@@ -56,18 +56,23 @@ typedef enum {
 } ckmpm_status;
 
 typedef enum { CKMPM_KERNEL_CK = 0, CKMPM_KERNEL_QUADRATIC = 1 } ckmpm_kernel;
-typedef enum { CKMPM_FIXED_COROTATED = 0, CKMPM_DRUCKER_PRAGER = 1 } ckmpm_model;
+typedef enum { CKMPM_FIXED_COROTATED = 0, CKMPM_DRUCKER_PRAGER = 1, CKMPM_J_FLUID = 2 } ckmpm_model;
 
 /* Constitutive parameters of one material.  Lame parameters are
  * mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu)).  Drucker-Prager
  * uses Hencky elasticity and the cone alpha = sqrt(2/3) 2 sin(phi)/(3 - sin(phi))
- * with cohesion 0 (klar2016, cited in Sec. 3.2). */
+ * with cohesion 0 (klar2016, cited in Sec. 3.2).  The J-based fluid (the
+ * equation of state of the dam-break scenes in the performance section) has
+ * pressure p = E (J^-gamma - 1), Kirchhoff stress -J p I, and keeps only its
+ * volume ratio: F = J^(1/3) I after every update; nu and friction_deg are
+ * unused for it. */
 typedef struct {
   int model;            /* ckmpm_model */
-  double E;             /* Young's modulus [Pa] */
+  double E;             /* Young's modulus [Pa]; for the fluid the equation-of-state constant B [Pa] */
   double nu;            /* Poisson ratio */
   double rho;           /* density [kg/m^3]; particle mass = rho * dx^3 / ppc */
   double friction_deg;  /* Drucker-Prager friction angle phi [deg] */
+  double gamma;         /* fluid equation-of-state exponent (unused by the solids) */
 } ckmpm_material;
 
 /* One simulation ("scene"): a cubic domain [0, res*dx]^3, y up. */

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libckmpm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ENONFINITE, ETIMEOUT, EBUSY, ENOTFOUND = range(9)
 KERNEL_CK, KERNEL_QUADRATIC = 0, 1
-FIXED_COROTATED, DRUCKER_PRAGER = 0, 1
+FIXED_COROTATED, DRUCKER_PRAGER, J_FLUID = 0, 1, 2
 FIELD_X, FIELD_V, FIELD_B, FIELD_C, FIELD_F, FIELD_E = 0, 1, 2, 3, 4, 5
 FIELD_GRID_M, FIELD_GRID_P, FIELD_GRID_V = 16, 17, 18
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "ENONFINITE", "ETIMEOUT", "EBUSY", "ENOTFOUND"]
@@ -27,7 +27,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "ENONFINITE", "ETI
 
 class ckmpm_material(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double),
-                ("rho", ctypes.c_double), ("friction_deg", ctypes.c_double)]
+                ("rho", ctypes.c_double), ("friction_deg", ctypes.c_double), ("gamma", ctypes.c_double)]
 
 
 class ckmpm_scene(ctypes.Structure):
@@ -234,7 +234,8 @@ def make_scene(res: int, dx: float, dt: float, materials, x, v=None, mat=None, g
     n = (x.shape[0] if hasattr(x, "shape") else len(x))
     mats = (ckmpm_material * len(materials))()
     for i, m in enumerate(materials):
-        mats[i] = ckmpm_material(int(m.model), float(m.E), float(m.nu), float(m.rho), float(m.friction_deg))
+        mats[i] = ckmpm_material(int(m.model), float(m.E), float(m.nu), float(m.rho), float(m.friction_deg),
+                                 float(getattr(m, "gamma", 7.15)))
     keep.append(mats)
     sc = ckmpm_scene()
     sc.n = int(n)

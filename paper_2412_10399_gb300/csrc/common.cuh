@@ -50,13 +50,14 @@ struct SceneDev {
 };
 
 struct MatDev {
-  int model;      // 0 fixed-corotated, 1 Drucker-Prager
+  int model;      // 0 fixed-corotated, 1 Drucker-Prager, 2 J-based fluid
   int scene;      // owning scene slot
   float mu, lam;  // Lame parameters
   float mass;     // rho * V0
   float alpha;    // Drucker-Prager cone coefficient
   float dpc;      // Drucker-Prager: (3 lam + 2 mu) / (2 mu) alpha = alpha (1 + nu) / (1 - 2 nu), any E
-  float E, nu;    // for per-particle E
+  float E, nu;    // for per-particle E; the fluid's equation-of-state constant B is E
+  float gamma;    // fluid equation-of-state exponent
 };
 
 // Pointers to one buffer of the particle pool.

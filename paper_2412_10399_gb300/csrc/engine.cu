@@ -380,7 +380,8 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
     return fail(ctx, CKMPM_EINVAL, "scene needs 1..255 materials");
   for (int i = 0; i < s->n_materials; ++i) {
     const ckmpm_material& m = s->materials[i];
-    if (m.model != 0 && m.model != 1) return fail(ctx, CKMPM_EINVAL, "material.model must be 0 or 1");
+    if (m.model < 0 || m.model > 2) return fail(ctx, CKMPM_EINVAL, "material.model must be 0, 1 or 2");
+    if (m.model == 2 && !(m.gamma > 0)) return fail(ctx, CKMPM_EINVAL, "fluid material needs gamma > 0");
     if (!(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0))
       return fail(ctx, CKMPM_EINVAL, "material needs E >= 0, -1 < nu < 0.5, rho > 0");
   }
@@ -628,6 +629,7 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
     double s = std::sin(m.friction_deg * M_PI / 180.0);
     md.alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s));
     md.dpc = (float)((double)md.alpha * (1.0 + m.nu) / (1.0 - 2.0 * m.nu));
+    md.gamma = (float)m.gamma;
     md.E = (float)m.E;
     md.nu = (float)m.nu;
   }

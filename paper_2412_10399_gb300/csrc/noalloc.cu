@@ -98,7 +98,8 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   if (!sc->materials || sc->n_materials < 1 || sc->n_materials > kStaticMaxMats) return CKMPM_EINVAL;
   for (int i = 0; i < sc->n_materials; ++i) {
     const ckmpm_material& m = sc->materials[i];
-    if ((m.model != 0 && m.model != 1) || !(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0))
+    if (m.model < 0 || m.model > 2 || !(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0) ||
+        (m.model == 2 && !(m.gamma > 0)))
       return CKMPM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -200,6 +201,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
     double s = std::sin(m.friction_deg * M_PI / 180.0);
     hm[i].alpha = (float)(std::sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s));
     hm[i].dpc = (float)((double)hm[i].alpha * (1.0 + m.nu) / (1.0 - 2.0 * m.nu));
+    hm[i].gamma = (float)m.gamma;
     hm[i].E = (float)m.E;
     hm[i].nu = (float)m.nu;
     mmax = std::max(mmax, m.rho * V0);

@@ -30,6 +30,8 @@ struct Num<float> {
   __device__ static __forceinline__ float abs_(float x) { return fabsf(x); }
   __device__ static __forceinline__ float log_(float x) { return logf(x); }
   __device__ static __forceinline__ float exp_(float x) { return expf(x); }
+  __device__ static __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+  __device__ static __forceinline__ float cbrt_(float x) { return cbrtf(x); }
   static constexpr int sweeps = 4;
   static constexpr float eps = 5.9604645e-8f;  // 2^-24
 };
@@ -40,6 +42,8 @@ struct Num<double> {
   __device__ static __forceinline__ double abs_(double x) { return fabs(x); }
   __device__ static __forceinline__ double log_(double x) { return log(x); }
   __device__ static __forceinline__ double exp_(double x) { return exp(x); }
+  __device__ static __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+  __device__ static __forceinline__ double cbrt_(double x) { return cbrt(x); }
   static constexpr int sweeps = 6;
   static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
 };
@@ -494,6 +498,29 @@ __device__ __forceinline__ void dp_small_strain(float* F, const float* X, float 
   tau[1] = tau[3] = m2 * Ln[3];
   tau[2] = tau[6] = m2 * Ln[4];
   tau[5] = tau[7] = m2 * Ln[5];
+}
+
+// J-based fluid (the equation of state of the dam-break scenes): J = det F,
+// pressure p = B (J^-gamma - 1), Kirchhoff stress tau = -J p I.
+template <typename T>
+__device__ __forceinline__ T det3(const T* F) {
+  return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) + F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+template <typename T>
+__device__ __forceinline__ void fluid_tau_of_J(T J, T Bk, T gamma, T* tau) {
+  const T s = -J * Bk * (Num<T>::pow_(J, -gamma) - T(1));
+#pragma unroll
+  for (int q = 0; q < 9; ++q) tau[q] = (q % 4 == 0) ? s : T(0);
+}
+// The fluid's update after F' = (I + dt C) F: it keeps only the volume ratio,
+// F <- J^(1/3) I, and its stress depends on J alone.
+template <typename T>
+__device__ __forceinline__ void fluid_update(T* F, T Bk, T gamma, T* tau) {
+  const T J = det3(F);
+  const T c = Num<T>::cbrt_(J);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) F[q] = (q % 4 == 0) ? c : T(0);
+  fluid_tau_of_J(J, Bk, gamma, tau);
 }
 
 // Kirchhoff stress of a given F without plasticity (used by readback/upload).

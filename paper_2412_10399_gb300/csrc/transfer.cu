@@ -665,7 +665,10 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       float Xs[6];
       const bool small_dp = mt.model == 1 && s.gap_tol <= 0.f && s.j_tol < 0.9f && s.cond_tol < 0.9f &&
                             left_strain(F, Xs) <= (1.f / 48.f);
-      if (small_dp) {
+      if (mt.model == 2) {
+        // J-based fluid: volume ratio only, stress from J (no decomposition)
+        fluid_update<float>(F, mt.E, mt.gamma, tau);
+      } else if (small_dp) {
         dp_small_strain(F, Xs, mu, lam, mt.dpc, tau);
       } else {
         // b = F F^T = U diag(sigma^2) U^T
@@ -815,6 +818,14 @@ __global__ void k_clear_gacc(StepView v) {
 
 // ------------------------------------------------------- readback / upload
 
+// Kirchhoff stress of a stored F (no plasticity), any material.
+__device__ __forceinline__ void stress_of(const MatDev& mt, const float* F, float mu, float lam, float* tau) {
+  if (mt.model == 2)
+    fluid_tau_of_J<float>(det3(F), mt.E, mt.gamma, tau);
+  else
+    stress_only<float>(mt.model, F, mu, lam, tau);
+}
+
 __device__ __forceinline__ void load_F(const Pool& P, uint32_t t, float* F) {
   float4 a = P.F0[t], b = P.F1[t];
   F[0] = a.x; F[1] = a.y; F[2] = a.z; F[3] = a.w;
@@ -853,7 +864,7 @@ __device__ __forceinline__ void recover_B(const Pool& P, const SceneDev& s, cons
   load_M(P, t, M);
   float mu, lam;
   lame_of(mt, P, t, mu, lam);
-  stress_only<float>(mt.model, F, mu, lam, tau);
+  stress_of(mt, F, mu, lam, tau);
   float dtv = s.dt * s.V0, im = 1.0f / mt.mass;
 #pragma unroll
   for (int q = 0; q < 9; ++q) B[q] = (M[q] + dtv * tau[q]) * im;
@@ -917,7 +928,7 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
       float F[9], tau[9], M[9], mu, lam;
       load_F(P, t, F);
       lame_of(mt, P, t, mu, lam);
-      stress_only<float>(mt.model, F, mu, lam, tau);
+      stress_of(mt, F, mu, lam, tau);
       for (int q = 0; q < 9; ++q) M[q] = mt.mass * in[9 * id + q] - dtv * tau[q];
       store_M(P, t, M);
     } else if (field == 4 || field == 5) {
@@ -933,7 +944,7 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
       float F[9], tau[9], M[9], mu, lam;
       load_F(P, t, F);
       lame_of(mt, P, t, mu, lam);
-      stress_only<float>(mt.model, F, mu, lam, tau);
+      stress_of(mt, F, mu, lam, tau);
       for (int q = 0; q < 9; ++q) M[q] = mt.mass * B[q] - dtv * tau[q];
       store_M(P, t, M);
     }

@@ -35,6 +35,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # Material models understood by both the CUDA path and the oracle.
 FIXED_COROTATED = 0
 DRUCKER_PRAGER = 1
+J_FLUID = 2
 
 # Transfer kernels.
 KERNEL_CK = 0          # the paper's compact kernel on the dual staggered grid
@@ -69,11 +70,12 @@ def normal(counter: np.ndarray, seed: int) -> np.ndarray:
 @dataclasses.dataclass
 class Material:
     """Constitutive parameters of one material (SI units)."""
-    model: int               # FIXED_COROTATED or DRUCKER_PRAGER
-    E: float                 # Young's modulus [Pa]
+    model: int               # FIXED_COROTATED, DRUCKER_PRAGER or J_FLUID
+    E: float                 # Young's modulus [Pa]; for the fluid the equation-of-state constant B [Pa]
     nu: float                # Poisson ratio
     rho: float               # density [kg/m^3]
     friction_deg: float = 0.0  # Drucker-Prager friction angle [deg]
+    gamma: float = 7.15      # fluid equation-of-state exponent
 
 
 @dataclasses.dataclass
@@ -186,6 +188,9 @@ def sample_cells(cells: np.ndarray, res: int, dx: float, seed: int) -> np.ndarra
 ELASTIC = Material(FIXED_COROTATED, 1e5, 0.3, 1000.0)
 SAND = Material(DRUCKER_PRAGER, 3.5e5, 0.3, 1600.0, 30.0)
 STIFF_BALL = Material(FIXED_COROTATED, 1e7, 0.3, 1e4)
+# J-based fluid of the dam-break scenes: B = 10 Pa, gamma = 7.15 (the paper's
+# parameters; its density is not stated, water's is used)
+FLUID = Material(J_FLUID, 10.0, 0.0, 1000.0, 0.0, 7.15)
 
 
 def elastic_cube(seed: int = 0, res: int = 64) -> Scene:
@@ -239,6 +244,25 @@ def large_impact(seed: int = 0) -> Scene:
     x = np.concatenate(xs)
     return Scene("large_impact", res, dx, 2e-5, x, np.concatenate(vs),
                  np.concatenate(ms), [SAND, STIFF_BALL], steps=200)
+
+
+def dam_break(n: int = 4175808, seed: int = 0, res: int = 256) -> Scene:
+    """A single dam break: n particles of J-based fluid uniform at random in a
+    cuboid against the x = 0 and z = 0 walls of a res^3 grid (dx = 1/res), at 8
+    particles per cell on average (width 96 cells for n <= 5e6, else 128; the
+    height follows from n).  The paper's performance section runs 4,175,808 and
+    8,994,048 particles on 256^3; dt 1e-4."""
+    dx = 1.0 / res
+    w = 96.0 if n <= 5_000_000 else 128.0
+    h = n / 8.0 / (w * w)
+    lo = 4.0
+    if lo + max(w, h) > res - 4:
+        raise ValueError("dam-break cuboid does not fit the grid")
+    ctr = np.arange(3 * n, dtype=np.uint64) + np.uint64(1 << 50)
+    u = uniform01(ctr, seed).reshape(n, 3)
+    x = (lo + u * np.array([w, h, w])) * dx
+    return Scene(f"dam_break_{n}", res, dx, 1e-4, x, np.zeros_like(x), np.zeros(n, np.uint8), [FLUID],
+                 steps=200)
 
 
 def differentiable_cube(seed: int = 0, res: int = 128, lo: int = 48, hi: int = 80) -> Scene:

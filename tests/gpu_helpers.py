@@ -25,7 +25,7 @@ def random_scene(n, res, seed, model=S.FIXED_COROTATED, kernel=S.KERNEL_CK, dt=1
     """A scene with a random (x, v, B, F) state, all rounded to float32."""
     x, v, B, F = S.random_state(n, res, seed, margin_cells=4.0, v_scale=v_scale, b_scale=b_scale,
                                 f_scale=f_scale, box=box)
-    mat = S.Material(model, E, 0.3, 1000.0 if model == S.FIXED_COROTATED else 1600.0, 30.0)
+    mat = S.Material(model, E, 0.3, 1600.0 if model == S.DRUCKER_PRAGER else 1000.0, 30.0)
     sc = S.Scene("random", res, 1.0 / res, dt, f32(x).astype(np.float64), f32(v).astype(np.float64),
                  np.zeros(n, np.uint8), [mat], gravity=gravity, bc_cells=bc_cells, kernel=kernel)
     return sc, f32(B), f32(F)

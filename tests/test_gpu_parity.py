@@ -109,6 +109,48 @@ def test_one_step_particle_parity(kernel, model, f_scale):
     assert rel(got[ck.FIELD_C], C.numpy()) <= 1e-4
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fluid_one_step_particle_parity(kernel):
+    """J-based fluid (B = 1e4 Pa so the pressure force is felt; F within 5% of
+    I, so J covers compression and expansion): one step against the oracle,
+    including the projection of F onto J^(1/3) I."""
+    ck = need_gpu()
+    sc, B, F = random_scene(5000, 32, 21, model=S.J_FLUID, kernel=kernel, E=1e4, f_scale=0.05)
+    sim = _sim(ck, sc, B, F)
+    sim.step(1)
+    sim.sync()
+    got = {f: sim.read(f) for f in (ck.FIELD_X, ck.FIELD_V, ck.FIELD_B, ck.FIELD_F)}
+    sim.close()
+    new = O.step(oracle_state(sc, B, F), O.params_from_scene(sc))
+    assert np.abs(got[ck.FIELD_X] - new.x.numpy()).max() <= 1e-6 * sc.dx + 2e-7
+    assert rel(got[ck.FIELD_V], new.v.numpy()) <= 2e-5
+    assert rel(got[ck.FIELD_F], new.F.numpy()) <= 2e-6
+    assert rel(got[ck.FIELD_B], new.B.numpy()) <= 5e-5
+    off = got[ck.FIELD_F] - np.einsum("nii->ni", got[ck.FIELD_F])[:, :, None] * np.eye(3)[None]
+    assert np.abs(off).max() == 0.0
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fluid_dam_break_40_steps_positions(kernel):
+    """A small dam break (24,576 fluid particles uniform in a 16 x 12 x 16-cell
+    cuboid on 64^3, the paper's B = 10 Pa and gamma = 7.15, dt 1e-4): positions
+    within 1e-3 dx of the oracle after 40 steps from the same initial state."""
+    ck = need_gpu()
+    res, n = 64, 16 * 12 * 16 * 8
+    dx = 1.0 / res
+    u = S.uniform01(np.arange(3 * n, dtype=np.uint64) + np.uint64(1 << 50), 3).reshape(n, 3)
+    x = (4.0 + u * np.array([16.0, 12.0, 16.0])) * dx
+    sc = S.Scene("small_dam_break", res, dx, 1e-4, f32(x).astype(np.float64), np.zeros_like(x), np.zeros(n, np.uint8),
+                 [S.FLUID], kernel=kernel)
+    sim = ck.Simulation(sc, kernel)
+    sim.step(40)
+    sim.sync()
+    xg = sim.read(ck.FIELD_X)
+    sim.close()
+    st = O.run(O.state_from_scene(sc), O.params_from_scene(sc), 40)
+    assert np.abs(xg - st.x.numpy()).max() <= 1e-3 * dx
+
+
 def test_elastic_cube_100_steps_positions():
     """Configuration 1 (32,768 particles, 64^3, dt 1e-4): positions within
     1e-3 dx of the FP64 oracle after 100 steps from the same initial state."""

@@ -46,3 +46,12 @@ def test_served_mix_shapes():
         assert 5e3 < r.scene.n < 2.2e6
         u = r.scene.x / r.scene.dx
         assert u.min() > 3.0 and u.max() < r.scene.res - 3.0
+
+
+def test_dam_break_counts_and_bounds():
+    for n in (4175808, 8994048):
+        sc = S.dam_break(n)
+        assert sc.n == n and sc.res == 256
+        u = sc.x / sc.dx
+        assert u.min() >= 4.0 and u[:, 1].max() < 4.0 + n / 8.0 / (96.0 if n <= 5_000_000 else 128.0) ** 2
+        assert sc.materials[0].model == S.J_FLUID

@@ -293,6 +293,36 @@ def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0, budget
     return st
 
 
+# The paper's G2P2G kernel times per substep for the dam-break scenes (its
+# performance table; RTX 3090, CK and the quadratic kernel of Wang 2020), for
+# context only: another machine and a fused kernel.
+PAPER_DAM_BREAK_MS = {4175808: {"ck": 2.9, "quadratic": 3.7}, 8994048: {"ck": 5.7, "quadratic": 7.2}}
+
+
+def dam_break_lines(ck, stream_ptr, warmup, steps, sizes=(4175808, 8994048)):
+    """The paper's dam-break workload (J-based fluid, 256^3): CK and quadratic
+    ms per step over the same steps, device-resident, no per-kernel events."""
+    from paper_2412_10399_gb300 import scenes as S
+    out = {}
+    for n in sizes:
+        sc = S.dam_break(n)
+        row = {}
+        for name, kernel in (("ck", ck.KERNEL_CK), ("quadratic", ck.KERNEL_QUADRATIC)):
+            ctx, keep = _make_ctx(ck, sc, kernel, stream_ptr)
+            ck.ckmpm_step(ctx, warmup)
+            ck.ckmpm_sync(ctx)
+            ms = _time_steps(ck, ctx, steps, stream_ptr)
+            ck.ckmpm_sync(ctx)
+            ck.ckmpm_destroy(ctx)
+            row[name] = {"ms_per_step": ms / steps, "value": n * steps / (ms / 1e3)}
+        row["ck_speedup"] = row["quadratic"]["ms_per_step"] / row["ck"]["ms_per_step"]
+        row["paper_g2p2g_ms_rtx3090"] = PAPER_DAM_BREAK_MS.get(n)
+        out[str(n)] = row
+    out["workload"] = ("J-based fluid (B = 10 Pa, gamma = 7.15, rho = 1000), uniform in a cuboid at 8 per cell, "
+                       f"256^3, dt 1e-4; steps {warmup}..{warmup + steps}")
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, local_rank, world = _env_rank()
@@ -397,6 +427,7 @@ def run_gpu(args):
            "how": "admit from pinned host x/v/mat, then per step: ckmpm_step + readback of positions to pinned host"}
 
     served = served_mix(ck, stream_ptr) if not args.no_served else None
+    dam = dam_break_lines(ck, stream_ptr, args.warmup, args.steps) if not args.no_dam else None
     cb = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:
@@ -411,7 +442,7 @@ def run_gpu(args):
                                     f"the keep from about step 73)",
                            "per_kernel_ms": "second run over the same steps with CUDA events around each launch"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "quadratic": quad, "served": served}
+                "clocks": clocks, "quadratic": quad, "served": served, "dam_break": dam}
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -430,6 +461,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-dam", action="store_true", help="skip the dam-break lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

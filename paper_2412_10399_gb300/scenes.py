@@ -265,6 +265,21 @@ def dam_break(n: int = 4175808, seed: int = 0, res: int = 256) -> Scene:
                  steps=200)
 
 
+def diffusion_bar(seed: int = 0, res: int = 256) -> Scene:
+    """The numerical-diffusion scene of the paper's comparisons: a 20 x 10 x
+    140-cell cuboid (dx = 1/256) with the high-frequency initial velocity
+    v_y = 0.2 sin(500 z), no gravity, dt 2e-5, 500 steps (100 frames at 10 kHz).
+    The paper does not give the material; the elastic cube's is used."""
+    dx = 1.0 / res
+    lo = np.array([118, 123, 58])
+    cells = filled_cells([_box(lo.tolist(), (lo + np.array([20, 10, 140])).tolist())], res)
+    x = sample_cells(cells, res, dx, seed)
+    v = np.zeros_like(x)
+    v[:, 1] = 0.2 * np.sin(500.0 * x[:, 2])
+    return Scene("diffusion_bar", res, dx, 2e-5, x, v, np.zeros(len(x), np.uint8), [ELASTIC],
+                 gravity=(0.0, 0.0, 0.0), steps=500)
+
+
 def differentiable_cube(seed: int = 0, res: int = 128, lo: int = 48, hi: int = 80) -> Scene:
     """Elastic cube cells [48,80)^3 on 128^3 (262,144 particles) with initial
     velocity (0.5, 0, 0) + N(0, 0.5^2) per component."""

@@ -42,6 +42,11 @@ Readings where the paper is silent or garbled (each one is a named choice):
      particle keeps only its volume ratio, F <- J^(1/3) I after each F update
      (the shear part of F carries no stress in a fluid).  The paper lists a
      viscosity 0.1 without its discretisation; it is not modelled.
+  R16 PIC transfer (Sec. 4.3 as written, the scheme of the paper's Taichi
+     comparison): P2G carries m v only, the force is f_i = -sum_p V0 tau_p
+     grad w_ip (R4's sign) with the gradient of the kernel itself,
+     grad w_ip = d w_ip / d x_p; G2P gives v_p (R5) and grad v_p = 1/2
+     sum_k sum_i v~_i (grad w_ip)^T for the F update; B stays 0.
   Quadratic comparison path: hu2018 MLS-MPM on one grid with the quadratic
   B-spline, D = dx^2/4 I.
 """
@@ -61,6 +66,8 @@ DRUCKER_PRAGER = 1
 J_FLUID = 2
 KERNEL_CK = 0
 KERNEL_QUADRATIC = 1
+TRANSFER_APIC_MLS = 0   # APIC momentum with the MLS force (Sec. 4.4, 4.5): the default
+TRANSFER_PIC = 1        # the PIC scheme of Sec. 4.3 with the kernel gradient
 
 
 # -----------------------------------------------------------------------------
@@ -72,6 +79,21 @@ def K1(x: torch.Tensor) -> torch.Tensor:
     ax = x.abs()
     val = 1.0 - ax + torch.sin(TWO_PI * ax) / TWO_PI
     return torch.where(ax < 1.0, val, torch.zeros_like(val))
+
+
+def K1_prime(x: torch.Tensor) -> torch.Tensor:
+    """d K1 / dx = sgn(x) (cos(2 pi |x|) - 1) on |x| < 1; K1 is C^2, so K1' is 0 at 0 and at |x| = 1."""
+    ax = x.abs()
+    val = torch.sign(x) * (torch.cos(TWO_PI * ax) - 1.0)
+    return torch.where(ax < 1.0, val, torch.zeros_like(val))
+
+
+def quadratic_bspline_prime(x: torch.Tensor) -> torch.Tensor:
+    """d N / dx of the quadratic B-spline: -2x on |x| < 1/2, (|x| - 3/2) sgn(x) on |x| < 3/2."""
+    ax = x.abs()
+    inner = -2.0 * x
+    outer = (ax - 1.5) * torch.sign(x)
+    return torch.where(ax < 0.5, inner, torch.where(ax < 1.5, outer, torch.zeros_like(ax)))
 
 
 def quadratic_bspline(x: torch.Tensor) -> torch.Tensor:
@@ -138,6 +160,7 @@ class Params:
     bc_cells: float = 3.0
     ppc: int = 8
     kernel: int = KERNEL_CK
+    transfer: int = TRANSFER_APIC_MLS
 
     @property
     def V0(self) -> float:
@@ -359,6 +382,20 @@ def plasticity(F: torch.Tensor, st: State, prm: Params) -> torch.Tensor:
 # transfers
 # -----------------------------------------------------------------------------
 
+def stencil_grad(x: torch.Tensor, dx: float, kernel: int, k: int):
+    """Kernel gradient grad w_ip = d w_ip / d x_p for the stencil of `stencil`
+    (same node order), shape (N,S,3): with w = prod_a K((x_i - x_p)_a / dx),
+    d w / d x_p,a = -K'((x_i - x_p)_a / dx) / dx * prod_{b != a} K((x_i - x_p)_b / dx)."""
+    idx, w, d = stencil(x, dx, kernel, k)
+    kern, kprime = (K1, K1_prime) if kernel == KERNEL_CK else (quadratic_bspline, quadratic_bspline_prime)
+    t = d / dx
+    kv = kern(t)
+    kp = kprime(t)
+    g = torch.stack([-kp[..., 0] * kv[..., 1] * kv[..., 2], -kv[..., 0] * kp[..., 1] * kv[..., 2],
+                     -kv[..., 0] * kv[..., 1] * kp[..., 2]], -1) / dx
+    return idx, w, d, g
+
+
 def _check_domain(x: torch.Tensor, prm: Params):
     u = x / prm.dx
     if bool((u < 0.5).any()) or bool((u >= prm.res - 0.5).any()):
@@ -389,6 +426,8 @@ def p2g(st: State, prm: Params, newton=False, stress=True) -> Dict[int, Tuple[to
     _check_domain(st.x, prm)
     n = prm.n_nodes
     mp = particle_mass(st, prm)
+    if prm.transfer == TRANSFER_PIC:
+        return _p2g_pic(st, prm, mp, newton, stress)
     D = apic_D(st.x, prm)
     Dinv = torch.linalg.inv(D)
     tau = kirchhoff_stress(st, prm, newton) if stress else torch.zeros_like(st.F)
@@ -400,6 +439,23 @@ def p2g(st: State, prm: Params, newton=False, stress=True) -> Dict[int, Tuple[to
         m_contrib = (w * mp[:, None]).reshape(-1)
         p_contrib = w[..., None] * (mp[:, None, None] * st.v[:, None, :]
                                     + torch.einsum("nab,nsb->nsa", A, d))
+        m = torch.zeros(n ** 3, dtype=F64).index_add(0, lin, m_contrib)
+        p = torch.zeros(n ** 3, 3, dtype=F64).index_add(0, lin, p_contrib.reshape(-1, 3))
+        out[k] = (m, p)
+    return out
+
+
+def _p2g_pic(st: State, prm: Params, mp, newton, stress):
+    """Reading R16: m_i = sum w m_p, m_i v_i + dt f_i = sum w m_p v_p - dt sum V0 tau grad w."""
+    n = prm.n_nodes
+    tau = kirchhoff_stress(st, prm, newton) if stress else torch.zeros_like(st.F)
+    out = {}
+    for k in grid_ids(prm.kernel):
+        idx, w, d, g = stencil_grad(st.x, prm.dx, prm.kernel, k)
+        lin = _lin(idx, n).reshape(-1)
+        m_contrib = (w * mp[:, None]).reshape(-1)
+        p_contrib = (w[..., None] * mp[:, None, None] * st.v[:, None, :]
+                     - prm.dt * prm.V0 * torch.einsum("nab,nsb->nsa", tau, g))
         m = torch.zeros(n ** 3, dtype=F64).index_add(0, lin, m_contrib)
         p = torch.zeros(n ** 3, 3, dtype=F64).index_add(0, lin, p_contrib.reshape(-1, 3))
         out[k] = (m, p)
@@ -442,6 +498,14 @@ def g2p(st: State, vgrid, prm: Params):
         B = B + torch.einsum("ns,nsa,nsb->nab", w, vi, d)
     v = v / len(ks)
     B = B / len(ks)
+    if prm.transfer == TRANSFER_PIC:
+        # reading R16: grad v = 1/2 sum_k sum_i v~_i grad w_ip^T, and B = 0
+        C = torch.zeros(N, 3, 3, dtype=F64)
+        for k in ks:
+            idx, _, _, g = stencil_grad(st.x, prm.dx, prm.kernel, k)
+            vi = vgrid[k][_lin(idx, n)]
+            C = C + torch.einsum("nsa,nsb->nab", vi, g)
+        return v, torch.zeros_like(B), C / len(ks)
     Dinv = torch.linalg.inv(apic_D(st.x, prm))
     return v, B, B @ Dinv
 
@@ -508,7 +572,7 @@ def params_from_scene(sc) -> Params:
     """Build oracle parameters from a scene description (duck-typed)."""
     mats = [Mat(m.model, m.E, m.nu, m.rho, m.friction_deg, getattr(m, "gamma", 7.15)) for m in sc.materials]
     return Params(res=sc.res, dx=sc.dx, dt=sc.dt, materials=mats, gravity=tuple(sc.gravity),
-                  bc_cells=sc.bc_cells, ppc=sc.ppc, kernel=sc.kernel)
+                  bc_cells=sc.bc_cells, ppc=sc.ppc, kernel=sc.kernel, transfer=getattr(sc, "transfer", 0))
 
 
 def state_from_scene(sc, x32=True) -> State:

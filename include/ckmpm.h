@@ -56,6 +56,18 @@ typedef enum {
 } ckmpm_status;
 
 typedef enum { CKMPM_KERNEL_CK = 0, CKMPM_KERNEL_QUADRATIC = 1 } ckmpm_kernel;
+
+/* Transfer scheme, OR-ed into a kernel argument (ckmpm_create, ckmpm_config,
+ * ckmpm_p2g_grids_static); fixed for a context.
+ *   CKMPM_TRANSFER_APIC_MLS (0, the default): APIC momentum with the MLS
+ *     force, state B (Sec. 4.4, 4.5).
+ *   CKMPM_TRANSFER_PIC: the PIC scheme of Sec. 4.3 with the kernel gradient
+ *     grad w_ip = d w_ip / d x_p: P2G adds w m v - dt V0 tau grad w to node
+ *     momentum; G2P gives v_p = 1/2 sum_k sum_i w v~_i and
+ *     grad v_p = 1/2 sum_k sum_i v~_i (grad w_ip)^T for F <- (I + dt grad v) F.
+ *     The state keeps no B: readback of B and C gives zeros and uploading B
+ *     is EINVAL. */
+typedef enum { CKMPM_TRANSFER_APIC_MLS = 0, CKMPM_TRANSFER_PIC = 2 } ckmpm_transfer;
 typedef enum { CKMPM_FIXED_COROTATED = 0, CKMPM_DRUCKER_PRAGER = 1, CKMPM_J_FLUID = 2 } ckmpm_model;
 
 /* Constitutive parameters of one material.  Lame parameters are
@@ -110,7 +122,7 @@ typedef struct {
 /* Capacities of a multi-scene context (a "server"): all resident scenes step
  * together in one launch per kernel over their concatenated block lists. */
 typedef struct {
-  int kernel;                  /* ckmpm_kernel; fixed for the context */
+  int kernel;                  /* ckmpm_kernel | ckmpm_transfer; fixed for the context */
   int64_t max_particles;       /* particle pool capacity */
   int64_t max_keys;            /* particle-block key space (sum over scenes of ceil(res/4)^3) */
   int64_t max_grid_blocks;     /* grid pool: 4x4x4-node blocks active at once, all scenes together */
@@ -154,7 +166,7 @@ typedef struct {
 } ckmpm_stats;
 
 /* Create a context holding one scene (scene id 0) with capacities equal to
- * that scene.  kernel: ckmpm_kernel.  stream: cudaStream_t or NULL.
+ * that scene.  kernel: ckmpm_kernel | ckmpm_transfer.  stream: cudaStream_t or NULL.
  * Errors: EINVAL (bad scene), ENOMEM, ECUDA.  *out is NULL on error. */
 CKMPM_API ckmpm_status ckmpm_create(const ckmpm_scene* scene, int kernel, void* stream, ckmpm_ctx** out);
 
@@ -259,8 +271,9 @@ CKMPM_API ckmpm_status ckmpm_diff_destroy(ckmpm_diff* d);
  * loads the library until the process exits.
  *   scene   is_device must be 1 (x, v, mat already on the current device);
  *           n <= 65536, res <= 64, n_materials <= 16, else CKMPM_EINVAL.
- *   kernel  ckmpm_kernel.
- *   B, F    device arrays of n*9 floats (row-major) or NULL (B = 0, F = I).
+ *   kernel  ckmpm_kernel | ckmpm_transfer.
+ *   B, F    device arrays of n*9 floats (row-major) or NULL (B = 0, F = I);
+ *           B must be NULL with CKMPM_TRANSFER_PIC.
  *   grid_m  device output, (res+1)^3 floats per grid (G- then G+ for CK).
  *   grid_p  device output, (res+1)^3 * 3 floats per grid.
  *   stream  cudaStream_t or NULL; the call returns after the work finished.

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libckmpm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ENONFINITE, ETIMEOUT, EBUSY, ENOTFOUND = range(9)
 KERNEL_CK, KERNEL_QUADRATIC = 0, 1
+TRANSFER_APIC_MLS, TRANSFER_PIC = 0, 2  # OR-ed into a kernel argument
 FIXED_COROTATED, DRUCKER_PRAGER, J_FLUID = 0, 1, 2
 FIELD_X, FIELD_V, FIELD_B, FIELD_C, FIELD_F, FIELD_E = 0, 1, 2, 3, 4, 5
 FIELD_GRID_M, FIELD_GRID_P, FIELD_GRID_V = 16, 17, 18
@@ -284,6 +285,12 @@ def torch_allocator():
 _FIELD_SHAPE = {FIELD_X: (3,), FIELD_V: (3,), FIELD_B: (3, 3), FIELD_C: (3, 3), FIELD_F: (3, 3), FIELD_E: ()}
 
 
+def kernel_code(scene) -> int:
+    """The C ABI's kernel argument for a scene: its kernel, with
+    TRANSFER_PIC when the scene asks for the PIC transfer (scene.transfer 1)."""
+    return int(scene.kernel) | (TRANSFER_PIC if getattr(scene, "transfer", 0) == 1 else 0)
+
+
 class Simulation:
     """One scene in its own context (thin wrapper over the C calls)."""
 
@@ -320,7 +327,7 @@ class Simulation:
 
     def read(self, field: int, scene_id: int = 0) -> np.ndarray:
         if field >= FIELD_GRID_M:
-            ng = 2 if self.kernel == KERNEL_CK else 1
+            ng = 2 if (self.kernel & 1) == KERNEL_CK else 1
             nn = self.res + 1
             shape = (ng, nn, nn, nn) if field == FIELD_GRID_M else (ng, nn, nn, nn, 3)
         else:

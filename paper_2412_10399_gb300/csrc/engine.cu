@@ -83,7 +83,8 @@ struct PendingFree {
 }  // namespace
 
 struct ckmpm_ctx {
-  int kind = 0;
+  int kind = 0;      // 0 CK, 1 quadratic
+  bool pic = false;  // PIC transfer
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   ckmpm_allocator alloc{};
@@ -390,8 +391,10 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
 }
 
 ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
-  ctx->kind = cfg->kernel;
-  if (ctx->kind != 0 && ctx->kind != 1) return fail(ctx, CKMPM_EINVAL, "kernel must be 0 (CK) or 1 (quadratic)");
+  if (cfg->kernel < 0 || cfg->kernel > 3)
+    return fail(ctx, CKMPM_EINVAL, "kernel must be 0 (CK) or 1 (quadratic), optionally | CKMPM_TRANSFER_PIC");
+  ctx->kind = cfg->kernel & 1;
+  ctx->pic = (cfg->kernel & CKMPM_TRANSFER_PIC) != 0;
   if (cfg->max_particles < 1 || cfg->max_keys < 1 || cfg->max_grid_blocks < 1 || cfg->max_virtual_blocks < 1 ||
       cfg->max_scenes < 1 ||
       cfg->max_scenes > 1024 || cfg->max_materials < 1 || cfg->max_materials > 65535)
@@ -410,7 +413,8 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   if (const char* e = getenv("CKMPM_CTAS_PER_SM")) per_sm = std::max(1, atoi(e));
   ctx->lc.persistent_ctas = ctx->sm_count * per_sm;
   ctx->lc.sm_count = ctx->sm_count;
-  ctx->lc.g2p_minb = cfg->kernel == 0 ? 5 : 4;
+  ctx->lc.g2p_minb = ctx->kind == 0 ? 5 : 4;
+  ctx->lc.pic = ctx->pic;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
@@ -862,7 +866,7 @@ ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, 
       if (tmp) dev_free(ctx, tmp);
       return fail(ctx, CKMPM_EINVAL, "scene has no particles in the pool");
     }
-    ck::launch_read_particles(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id,
+    ck::launch_read_particles(ctx->kind, ctx->pic, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id,
                               (uint32_t)sg->start, (uint32_t)sg->n, field, out);
   }
   cudaError_t e = cudaGetLastError();
@@ -883,6 +887,7 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
         field == CKMPM_FIELD_E))
     return fail(ctx, CKMPM_EINVAL, "field cannot be uploaded");
   if (field == CKMPM_FIELD_E && !ctx->per_E) return fail(ctx, CKMPM_EINVAL, "context has no per-particle E");
+  if (field == CKMPM_FIELD_B && ctx->pic) return fail(ctx, CKMPM_EINVAL, "the PIC transfer keeps no B");
   const SceneHost& h = ctx->scenes[scene_id];
   size_t want = sizeof(float) * (size_t)(field_floats(field) * h.n);
   if (bytes != want) return fail(ctx, CKMPM_EINVAL, "upload size mismatch: expected " + std::to_string(want));
@@ -896,7 +901,7 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
     CK_TRY(cudaMemcpyAsync(tmp, src, want, cudaMemcpyHostToDevice, ctx->stream), "upload copy");
     in = (const float*)tmp;
   }
-  ck::launch_write_particles(ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id, (uint32_t)sg->start,
+  ck::launch_write_particles(ctx->pic, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id, (uint32_t)sg->start,
                              (uint32_t)sg->n, field, in);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

@@ -13,15 +13,16 @@ struct LaunchCfg {
   int persistent_ctas;  // CTAs of the persistent P2G / update / G2P launches
   int sm_count = 1;     // SMs of the device (grid of the float64 pass)
   int g2p_minb = 4;     // resident G2P warps per SM / 4 the register budget targets
+  bool pic = false;     // PIC transfer (kernel gradient) instead of APIC + MLS
 };
 
 enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4 };
 
 // transfer.cu
 void launch_transfer(int kind, const LaunchCfg& lc, const StepView& v, int which);
-void launch_read_particles(int kind, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
-                           uint32_t start, uint32_t n, int field, float* out);
-void launch_write_particles(cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
+void launch_read_particles(int kind, bool pic, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats,
+                           int scene, uint32_t start, uint32_t n, int field, float* out);
+void launch_write_particles(bool pic, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
                             uint32_t start, uint32_t n, int field, const float* in);
 void launch_read_grid(int kind, cudaStream_t st, const StepView& v, int scene, int which, float* out);
 void launch_admit(int kind, cudaStream_t st, Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd,

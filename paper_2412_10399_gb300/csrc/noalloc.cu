@@ -90,7 +90,10 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
                                                         const float* F, float* grid_m, float* grid_p,
                                                         void* stream) {
   if (!sc || !sc->x || !grid_m || !grid_p) return CKMPM_EINVAL;
-  if (kernel != 0 && kernel != 1) return CKMPM_EINVAL;
+  if (kernel < 0 || kernel > 3) return CKMPM_EINVAL;
+  const bool pic = (kernel & CKMPM_TRANSFER_PIC) != 0;
+  if (pic && B) return CKMPM_EINVAL;  // the PIC transfer keeps no B
+  kernel &= 1;
   if (!sc->is_device) return CKMPM_EINVAL;  // inputs must already be on the device
   if (sc->n < 1 || sc->n > kStaticMaxN) return CKMPM_EINVAL;
   if (sc->res < 4 || sc->res > kStaticMaxRes) return CKMPM_EINVAL;
@@ -230,8 +233,8 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   ck::launch_admit(kernel, st, P, v.key_cur, v.cnt_cur, v.bnd_cur, d_scene, d_mats, 0, 0u, (uint32_t)sc->n_materials,
                    0u, (uint32_t)n, sc->x, sc->v, sc->mat, nullptr, v.err);
   if (F || B) {
-    if (F) ck::launch_write_particles(st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_F, F);
-    if (B) ck::launch_write_particles(st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_B, B);
+    if (F) ck::launch_write_particles(pic, st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_F, F);
+    if (B) ck::launch_write_particles(pic, st, P, d_scene, d_mats, 0, 0u, (uint32_t)n, CKMPM_FIELD_B, B);
     // M changed: histogram and P2G bounds again
     CK_S(cudaMemsetAsync(v.cnt_cur, 0, sizeof(uint32_t) * nkeys, st));
     CK_S(cudaMemsetAsync(v.bnd_cur, 0, sizeof(uint32_t) * 2 * nkeys, st));
@@ -245,6 +248,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   ck::launch_bin(st, v, bs, ck::LB_SCATTER, (uint32_t)nvb, grid_ctas);
   ck::launch_bin(st, v, bs, ck::LB_GLIST, (uint32_t)nvb, grid_ctas);
   ck::LaunchCfg lc{st, sms * 8};
+  lc.pic = pic;
   ck::launch_transfer(kernel, lc, v, ck::LK_P2G);
   ck::launch_read_grid(kernel, st, v, 0, 0, grid_m);
   ck::launch_read_grid(kernel, st, v, 0, 1, grid_p);

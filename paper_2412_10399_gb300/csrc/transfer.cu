@@ -55,6 +55,26 @@ __device__ __forceinline__ float sin_2pi(float f) {
   return t * p;
 }
 
+// cos(2 pi f) for f in [0, 1): the reduction of sin_2pi, where the fold
+// t -> sign(t)/2 - t flips the cosine's sign, then the Taylor series of cos x
+// at x = 2 pi t, |x| <= pi/2, through x^12: coefficients
+// (-1)^k (2 pi)^(2k) / (2k)!, truncation error below (pi/2)^14 / 14! = 6.4e-9.
+__device__ __forceinline__ float cos_2pi(float f) {
+  float t = f - rintf(f);
+  const float h = copysignf(0.5f, t) - t;
+  const bool fold = fabsf(t) > 0.25f;
+  t = fold ? h : t;
+  const float t2 = t * t;
+  float p = 7.903536371318465f;
+  p = fmaf(p, t2, -26.426256783374388f);
+  p = fmaf(p, t2, 60.24464137187664f);
+  p = fmaf(p, t2, -85.45681720669371f);
+  p = fmaf(p, t2, 64.93939402266828f);
+  p = fmaf(p, t2, -19.739208802178716f);
+  p = fmaf(p, t2, 1.0f);
+  return fold ? -p : p;
+}
+
 // 1/x for a normal float x: the hardware approximation refined by one
 // Newton-Raphson step e = 1 - x y, y <- y + y e (the classical iteration for
 // the reciprocal; the error after one step is about the square of the
@@ -141,6 +161,7 @@ struct Sten<0> {
   float w[2][3][2];   // per slot, axis, node
   float d[2][3][2];
   float li[3], y[3], den;  // D^-1 = diag(li) - den y y^T (cells^-2)
+  float k[2][3][2];        // PIC transfer: K1'(d) per slot, axis, node (set_grad)
   __device__ __forceinline__ bool set(float ux, float uy, float uz, int ox, int oy, int oz) {
     float u[3] = {ux, uy, uz};
     int o[3] = {ox, oy, oz};
@@ -176,6 +197,19 @@ struct Sten<0> {
     den = rcp_nr(1.0f + s[0] * y[0] + s[1] * y[1] + s[2] * y[2]);
     return ok;
   }
+  // K1'(x) = sgn(x) (cos(2 pi |x|) - 1) at the node offsets d = -f, 1 - f:
+  // with c = cos(2 pi f+), 1 - c and c - 1 on G+; cos(2 pi f-) = -c, so
+  // 1 + c and -1 - c on G-.  Each pair sums to 0 (the weights sum to 1).
+  __device__ __forceinline__ void set_grad() {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float c = cos_2pi(-d[1][a][0]);
+      k[1][a][0] = 1.0f - c;
+      k[1][a][1] = c - 1.0f;
+      k[0][a][0] = 1.0f + c;
+      k[0][a][1] = -1.0f - c;
+    }
+  }
 };
 
 template <>
@@ -183,6 +217,7 @@ struct Sten<1> {
   int r[3];
   float w[3][3];
   float d[3][3];
+  float k[3][3];  // PIC transfer: N'(d) per axis, node (set_grad)
   __device__ __forceinline__ bool set(float ux, float uy, float uz, int ox, int oy, int oz) {
     float u[3] = {ux, uy, uz};
     int o[3] = {ox, oy, oz};
@@ -202,6 +237,17 @@ struct Sten<1> {
       d[a][2] = 2.0f - f;
     }
     return ok;
+  }
+  // N'(x) of the quadratic B-spline at d = -f, 1 - f, 2 - f (f in [1/2, 3/2)):
+  // 3/2 - f, 2 (f - 1), 1/2 - f.
+  __device__ __forceinline__ void set_grad() {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float f = -d[a][0];
+      k[a][0] = 1.5f - f;
+      k[a][1] = 2.0f * (f - 1.0f);
+      k[a][2] = 0.5f - f;
+    }
   }
 };
 
@@ -235,6 +281,51 @@ __device__ __forceinline__ void for_nodes(const Sten<1>& st, Fn&& fn) {
       int row = ((st.r[2] + sz) * 6 + (st.r[1] + sy)) * 6 + st.r[0];
 #pragma unroll
       for (int sx = 0; sx < 3; ++sx) fn(row + sx, st.w[0][sx] * wyz, st.d[0][sx], st.d[1][sy], st.d[2][sz]);
+    }
+}
+
+// PIC transfer: visit every (node, weight, kernel-derivative products) of a
+// stencil, fn(staged_index, w, gx, gy, gz) with w = Kx Ky Kz and
+// g = (K'x Ky Kz, Kx K'y Kz, Kx Ky K'z), so that grad w = -g / dx (the
+// gradient with respect to the particle position).  Needs set_grad().
+template <typename Fn>
+__device__ __forceinline__ void for_nodes_grad(const Sten<0>& st, Fn&& fn) {
+#pragma unroll
+  for (int slot = 0; slot < 2; ++slot) {
+    const int E = slot == 0 ? 5 : 6;
+    const int base = slot == 0 ? 0 : 125;
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+      for (int sy = 0; sy < 2; ++sy) {
+        const float wyz = st.w[slot][1][sy] * st.w[slot][2][sz];
+        const float kyz = st.k[slot][1][sy] * st.w[slot][2][sz];
+        const float ykz = st.w[slot][1][sy] * st.k[slot][2][sz];
+        const int row = base + ((st.r[slot][2] + sz) * E + (st.r[slot][1] + sy)) * E + st.r[slot][0];
+#pragma unroll
+        for (int sx = 0; sx < 2; ++sx) {
+          const float wx = st.w[slot][0][sx];
+          fn(row + sx, wx * wyz, st.k[slot][0][sx] * wyz, wx * kyz, wx * ykz);
+        }
+      }
+  }
+}
+
+template <typename Fn>
+__device__ __forceinline__ void for_nodes_grad(const Sten<1>& st, Fn&& fn) {
+#pragma unroll
+  for (int sz = 0; sz < 3; ++sz)
+#pragma unroll
+    for (int sy = 0; sy < 3; ++sy) {
+      const float wyz = st.w[1][sy] * st.w[2][sz];
+      const float kyz = st.k[1][sy] * st.w[2][sz];
+      const float ykz = st.w[1][sy] * st.k[2][sz];
+      const int row = ((st.r[2] + sz) * 6 + (st.r[1] + sy)) * 6 + st.r[0];
+#pragma unroll
+      for (int sx = 0; sx < 3; ++sx) {
+        const float wx = st.w[0][sx];
+        fn(row + sx, wx * wyz, st.k[0][sx] * wyz, wx * kyz, wx * ykz);
+      }
     }
 }
 
@@ -327,6 +418,75 @@ __device__ __forceinline__ void g2p_gather(const Sten<1>& st, const float4* sv, 
   }
 }
 
+// PIC transfer: S = sum w v~ and the derivative sums G_a = sum g_a v~ over one
+// grid's N^3 stencil (g as in for_nodes_grad), by the same x, y, z reduction
+// as gather_moments with the kernel derivative in place of the offset.
+template <int N, int E>
+__device__ __forceinline__ void gather_grad(const float4* sv, int base, const float* wx, const float* wy,
+                                            const float* wz, const float* kx, const float* ky, const float* kz,
+                                            float* S, float* Gx, float* Gy, float* Gz) {
+#pragma unroll
+  for (int sz = 0; sz < N; ++sz) {
+    float Ps[3], Px[3], Py[3];
+#pragma unroll
+    for (int sy = 0; sy < N; ++sy) {
+      float Rs[3], Rx[3];
+      const int row = base + (sz * E + sy) * E;
+#pragma unroll
+      for (int sx = 0; sx < N; ++sx) {
+        const float4 a = sv[row + sx];
+        const float t[3] = {a.x, a.y, a.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Rs[c] = sx == 0 ? wx[sx] * t[c] : fmaf(wx[sx], t[c], Rs[c]);
+          Rx[c] = sx == 0 ? kx[sx] * t[c] : fmaf(kx[sx], t[c], Rx[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Ps[c] = sy == 0 ? wy[sy] * Rs[c] : fmaf(wy[sy], Rs[c], Ps[c]);
+        Px[c] = sy == 0 ? wy[sy] * Rx[c] : fmaf(wy[sy], Rx[c], Px[c]);
+        Py[c] = sy == 0 ? ky[sy] * Rs[c] : fmaf(ky[sy], Rs[c], Py[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      S[c] = sz == 0 ? wz[sz] * Ps[c] : fmaf(wz[sz], Ps[c], S[c]);
+      Gx[c] = sz == 0 ? wz[sz] * Px[c] : fmaf(wz[sz], Px[c], Gx[c]);
+      Gy[c] = sz == 0 ? wz[sz] * Py[c] : fmaf(wz[sz], Py[c], Gy[c]);
+      Gz[c] = sz == 0 ? kz[sz] * Ps[c] : fmaf(kz[sz], Ps[c], Gz[c]);
+    }
+  }
+}
+
+// PIC transfer: v = h sum w v~ and Gr = h sum v~ g^T (row c, column a), so
+// that grad v = -Gr / dx; h = 1/2 averages the two CK grids.  Needs set_grad().
+__device__ __forceinline__ void g2p_gather_grad(const Sten<0>& st, const float4* sv, float* vel, float* Gr) {
+  float S[2][3], D[2][3][3];
+  gather_grad<2, 5>(sv, (st.r[0][2] * 5 + st.r[0][1]) * 5 + st.r[0][0], st.w[0][0], st.w[0][1], st.w[0][2],
+                    st.k[0][0], st.k[0][1], st.k[0][2], S[0], D[0][0], D[0][1], D[0][2]);
+  gather_grad<2, 6>(sv, 125 + (st.r[1][2] * 6 + st.r[1][1]) * 6 + st.r[1][0], st.w[1][0], st.w[1][1], st.w[1][2],
+                    st.k[1][0], st.k[1][1], st.k[1][2], S[1], D[1][0], D[1][1], D[1][2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vel[c] = 0.5f * (S[0][c] + S[1][c]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Gr[c * 3 + a] = 0.5f * (D[0][a][c] + D[1][a][c]);
+  }
+}
+
+__device__ __forceinline__ void g2p_gather_grad(const Sten<1>& st, const float4* sv, float* vel, float* Gr) {
+  float S[3], D[3][3];
+  gather_grad<3, 6>(sv, (st.r[2] * 6 + st.r[1]) * 6 + st.r[0], st.w[0], st.w[1], st.w[2], st.k[0], st.k[1],
+                    st.k[2], S, D[0], D[1], D[2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vel[c] = S[c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Gr[c * 3 + a] = D[a][c];
+  }
+}
+
 // R = scale Q D^-1 for a row-major 3x3 Q.  CK: D^-1 = diag(li) - den y y^T,
 // so each row costs one dot product with y and three fused updates instead of
 // a full 3x3 product; quadratic: D^-1 = 4 I.
@@ -404,6 +564,11 @@ struct P2GBound<1> {
 // wmax m |v|_inf + wd * dinv * max_row sum_k |M_rk| / dx, since
 // |w (A^ d)_r| <= sum_k |A^_rk| |w d_k| and the rows of A^ = M D^-1 / dx sum
 // to at most sum_j |M_rj| * dinv / dx.
+// The PIC transfer's contribution w m v + M grad w (M = -dt V0 tau) has the
+// same bound with wd * dinv replaced by the largest |g_a| of for_nodes_grad:
+// CK 2 (|K1'| <= 2, at |x| = 1/2, times weights <= 1), quadratic 0.5625
+// (|N'| <= 1 times 0.75^2); both are below wd * dinv (4.04 and 0.5644), so
+// one bound serves both transfers.
 // The particle's two bounds (mass, momentum) go into its block's entry of
 // the per-key bound table when it is binned (G2P for the next step, admission
 // and re-keying otherwise), so P2G reads a block's bounds without a pass over
@@ -443,7 +608,36 @@ __device__ __forceinline__ void p2g_scatter(const SceneDev& s, const MatDev* mat
   });
 }
 
+// PIC transfer (Sec. 4.3 with the kernel gradient): the state holds
+// M = -dt V0 tau (B = 0), and a node receives w m v + M grad w with
+// grad w = -g / dx, i.e. w m v + A g with A = -M / dx, pre-scaled.
 template <int KIND>
+__device__ __forceinline__ void p2g_scatter_pic(const SceneDev& s, const MatDev* mats, uint32_t* err,
+                                                const P2GPart& q, int ox, int oy, int oz, float Sm, float Sp,
+                                                int (*sm)[Geo<KIND>::NS]) {
+  Sten<KIND> st;
+  if (!st.set(q.X.x * s.inv_dx, q.X.y * s.inv_dx, q.X.z * s.inv_dx, ox, oy, oz)) {
+    flag_error(err, CK_ERR_INTERNAL);
+    return;
+  }
+  st.set_grad();
+  const float M[9] = {q.a.w, q.b.x, q.b.y, q.b.z, q.b.w, q.c.x, q.c.y, q.c.z, q.c.w};
+  const float sc = -s.inv_dx * Sp;
+  float A[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) A[r] = sc * M[r];
+  const float mass = mats[__float_as_uint(q.X.w)].mass;
+  const float ms = mass * Sm;
+  const float px = mass * q.a.x * Sp, py = mass * q.a.y * Sp, pz = mass * q.a.z * Sp;
+  for_nodes_grad(st, [&](int j, float w, float gx, float gy, float gz) {
+    atomicAdd(&sm[0][j], __float2int_rn(w * ms));
+    atomicAdd(&sm[1][j], __float2int_rn(fmaf(w, px, A[0] * gx + A[1] * gy + A[2] * gz)));
+    atomicAdd(&sm[2][j], __float2int_rn(fmaf(w, py, A[3] * gx + A[4] * gy + A[5] * gz)));
+    atomicAdd(&sm[3][j], __float2int_rn(fmaf(w, pz, A[6] * gx + A[7] * gy + A[8] * gz)));
+  });
+}
+
+template <int KIND, bool PIC>
 __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   constexpr uint32_t CAP = kP2GStage, C = kP2GStage / 32;
@@ -492,7 +686,13 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
 #pragma unroll 1
       for (uint32_t r = 0; r < C; ++r) {
         const uint32_t i = lane * C + r;
-        if (i < m) p2g_scatter<KIND>(s, v.mats, v.err, P2GPart{sX[i], sA[i], sB[i], sC[i]}, ox, oy, oz, Sm, Sp, sm);
+        if (i < m) {
+          const P2GPart q{sX[i], sA[i], sB[i], sC[i]};
+          if constexpr (PIC)
+            p2g_scatter_pic<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
+          else
+            p2g_scatter<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
+        }
       }
       __syncwarp();  // the next chunk overwrites the staged copies
     }
@@ -567,7 +767,7 @@ __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(
 constexpr int kG2PWarp = 32;
 __host__ __device__ constexpr int g2p_stage(int minb) { return minb >= 5 ? 64 : 128; }  // particles per chunk
 
-template <int KIND, int MINB>
+template <int KIND, int MINB, bool PIC>
 __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   constexpr int CAP = g2p_stage(MINB);
@@ -640,12 +840,20 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
         flag_error(v.err, CK_ERR_INTERNAL);
         continue;
       }
-      float vel[3], Bh[9];
-      g2p_gather(st, sv, vel, Bh);
+      float vel[3], Bh[9], G[9];
+      if constexpr (PIC) {
+        // grad v = -Gr / dx (Gr in Bh); F' = (I + dt grad v) F
+        st.set_grad();
+        g2p_gather_grad(st, sv, vel, Bh);
+        const float sc = -s.dt * s.inv_dx;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) G[q] = sc * Bh[q];
+      } else {
+        // C = B D^-1 = Bh D^-1 / dx ; F' = (I + dt C) F
+        g2p_gather(st, sv, vel, Bh);
+        mul_dinv(st, Bh, s.dt * s.inv_dx, G);
+      }
       const float vx = vel[0], vy = vel[1], vz = vel[2];
-      // C = B D^-1 = Bh D^-1 / dx ; F' = (I + dt C) F
-      float G[9];
-      mul_dinv(st, Bh, s.dt * s.inv_dx, G);
       G[0] += 1.0f;
       G[4] += 1.0f;
       G[8] += 1.0f;
@@ -701,11 +909,11 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
           constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, U, e, sg);
         }
       }
-      // M' = m B' - dt V0 tau, B' = dx Bh
+      // M' = m B' - dt V0 tau, B' = dx Bh (APIC) or 0 (PIC)
       const float mdx = mt.mass * s.dx, dtv = s.dt * s.V0;
       float Mn[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Mn[q] = mdx * Bh[q] - dtv * tau[q];
+      for (int q = 0; q < 9; ++q) Mn[q] = PIC ? -dtv * tau[q] : mdx * Bh[q] - dtv * tau[q];
       float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
       // next key; particles leaving the interior are clamped and flagged
       float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
@@ -870,9 +1078,10 @@ __device__ __forceinline__ void recover_B(const Pool& P, const SceneDev& s, cons
   for (int q = 0; q < 9; ++q) B[q] = (M[q] + dtv * tau[q]) * im;
 }
 
+// pic: the PIC transfer keeps B = 0, so B and C read as 0.
 template <int KIND>
 __global__ void k_read_particles(Pool P, const SceneDev* scenes, const MatDev* mats, int scene, uint32_t start,
-                                 uint32_t n, int field, float* out) {
+                                 uint32_t n, int field, int pic, float* out) {
   const SceneDev s = scenes[scene];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t t = start + i;
@@ -890,6 +1099,8 @@ __global__ void k_read_particles(Pool P, const SceneDev* scenes, const MatDev* m
       for (int q = 0; q < 9; ++q) out[9 * id + q] = F[q];
     } else if (field == 5) {
       out[id] = P.E ? P.E[t] : 0.f;
+    } else if (pic) {
+      for (int q = 0; q < 9; ++q) out[9 * id + q] = 0.f;
     } else {
       float B[9];
       recover_B(P, s, mt, t, B);
@@ -909,9 +1120,10 @@ __global__ void k_read_particles(Pool P, const SceneDev* scenes, const MatDev* m
   }
 }
 
-// Overwrite one field from original-order input; keeps M = m B - dt V0 tau(F).
+// Overwrite one field from original-order input; keeps M = m B - dt V0 tau(F)
+// (pic: B = 0, the host refuses uploads of B).
 __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* mats, int scene, uint32_t start,
-                                  uint32_t n, int field, const float* in) {
+                                  uint32_t n, int field, int pic, const float* in) {
   const SceneDev s = scenes[scene];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t t = start + i;
@@ -932,8 +1144,8 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
       for (int q = 0; q < 9; ++q) M[q] = mt.mass * in[9 * id + q] - dtv * tau[q];
       store_M(P, t, M);
     } else if (field == 4 || field == 5) {
-      float B[9];
-      recover_B(P, s, mt, t, B);
+      float B[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (!pic) recover_B(P, s, mt, t, B);
       if (field == 4) {
         P.F0[t] = make_float4(in[9 * id], in[9 * id + 1], in[9 * id + 2], in[9 * id + 3]);
         P.F1[t] = make_float4(in[9 * id + 4], in[9 * id + 5], in[9 * id + 6], in[9 * id + 7]);
@@ -1075,7 +1287,12 @@ __global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd, con
 template <int KIND>
 static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
-    case LK_P2G: k_p2g<KIND><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v); break;
+    case LK_P2G:
+      if (lc.pic)
+        k_p2g<KIND, true><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+      else
+        k_p2g<KIND, false><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+      break;
     // a wide grid: each CTA's block loop is short, so the dependent loads of
     // one block (list entry, scene, accumulators) overlap across CTAs
     case LK_UPDATE: k_grid_update<KIND><<<lc.sm_count * 64, 128, 0, lc.stream>>>(v); break;
@@ -1084,12 +1301,15 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
       // chunks) for the compact kernel and 16 (128 registers) for the
       // quadratic twin by default, the faster of each on the large-impact
       // scene; 24 (80 registers) on request.  One resident wave.
-      if (lc.g2p_minb >= 6)
-        k_g2p<KIND, 6><<<lc.sm_count * 24, kG2PWarp, 0, lc.stream>>>(v);
+      // The PIC transfer runs each kernel's default budget only.
+      if (lc.pic)
+        k_g2p<KIND, KIND == 0 ? 5 : 4, true><<<lc.sm_count * (KIND == 0 ? 20 : 16), kG2PWarp, 0, lc.stream>>>(v);
+      else if (lc.g2p_minb >= 6)
+        k_g2p<KIND, 6, false><<<lc.sm_count * 24, kG2PWarp, 0, lc.stream>>>(v);
       else if (lc.g2p_minb == 5)
-        k_g2p<KIND, 5><<<lc.sm_count * 20, kG2PWarp, 0, lc.stream>>>(v);
+        k_g2p<KIND, 5, false><<<lc.sm_count * 20, kG2PWarp, 0, lc.stream>>>(v);
       else
-        k_g2p<KIND, 4><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
+        k_g2p<KIND, 4, false><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
       break;
     case LK_G2P_FP64: k_g2p_fp64<KIND><<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
@@ -1103,23 +1323,23 @@ void launch_transfer(int kind, const LaunchCfg& lc, const StepView& v, int which
     launch_all<1>(lc, v, which);
 }
 
-void launch_read_particles(int kind, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
-                           uint32_t start, uint32_t n, int field, float* out) {
+void launch_read_particles(int kind, bool pic, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats,
+                           int scene, uint32_t start, uint32_t n, int field, float* out) {
   int blocks = (int)((n + 255) / 256);
   if (blocks < 1) blocks = 1;
   if (blocks > 4096) blocks = 4096;
   if (kind == 0)
-    k_read_particles<0><<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, out);
+    k_read_particles<0><<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, pic ? 1 : 0, out);
   else
-    k_read_particles<1><<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, out);
+    k_read_particles<1><<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, pic ? 1 : 0, out);
 }
 
-void launch_write_particles(cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
+void launch_write_particles(bool pic, cudaStream_t st, Pool P, const SceneDev* scenes, const MatDev* mats, int scene,
                             uint32_t start, uint32_t n, int field, const float* in) {
   int blocks = (int)((n + 255) / 256);
   if (blocks < 1) blocks = 1;
   if (blocks > 4096) blocks = 4096;
-  k_write_particles<<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, in);
+  k_write_particles<<<blocks, 256, 0, st>>>(P, scenes, mats, scene, start, n, field, pic ? 1 : 0, in);
 }
 
 void launch_read_grid(int kind, cudaStream_t st, const StepView& v, int scene, int which, float* out) {

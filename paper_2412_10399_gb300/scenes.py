@@ -41,6 +41,10 @@ J_FLUID = 2
 KERNEL_CK = 0          # the paper's compact kernel on the dual staggered grid
 KERNEL_QUADRATIC = 1   # quadratic B-spline MLS-MPM on one grid (comparison path)
 
+# Transfer schemes.
+TRANSFER_APIC_MLS = 0  # APIC momentum with the MLS force (Sec. 4.4, 4.5)
+TRANSFER_PIC = 1       # PIC of Sec. 4.3 with the kernel gradient
+
 
 def splitmix64(counter: np.ndarray, seed: int) -> np.ndarray:
     """SplitMix64 output for each uint64 counter (vectorised, wraps mod 2^64)."""
@@ -94,6 +98,7 @@ class Scene:
     ppc: int = 8               # particles per filled cell (sets V0 = dx^3/ppc)
     steps: int = 100
     kernel: int = KERNEL_CK
+    transfer: int = TRANSFER_APIC_MLS
 
     @property
     def n(self) -> int:

@@ -47,6 +47,10 @@ Readings where the paper is silent or garbled (each one is a named choice):
      grad w_ip (R4's sign) with the gradient of the kernel itself,
      grad w_ip = d w_ip / d x_p; G2P gives v_p (R5) and grad v_p = 1/2
      sum_k sum_i v~_i (grad w_ip)^T for the F update; B stays 0.
+  R17 APIC with the kernel gradient (Sec. 4.4 taken literally: its momentum
+     transfer and B update, "the rest as in the PIC scheme"): P2G carries
+     w m (v + B D^-1 (x_i - x_p)) and the force of R16; G2P gives v and B as
+     for APIC and the R16 grad v for the F update.
   Quadratic comparison path: hu2018 MLS-MPM on one grid with the quadratic
   B-spline, D = dx^2/4 I.
 """
@@ -68,6 +72,7 @@ KERNEL_CK = 0
 KERNEL_QUADRATIC = 1
 TRANSFER_APIC_MLS = 0   # APIC momentum with the MLS force (Sec. 4.4, 4.5): the default
 TRANSFER_PIC = 1        # the PIC scheme of Sec. 4.3 with the kernel gradient
+TRANSFER_APIC_GRAD = 2  # APIC momentum (Sec. 4.4) with the kernel-gradient force and grad v of Sec. 4.3
 
 
 # -----------------------------------------------------------------------------
@@ -426,7 +431,7 @@ def p2g(st: State, prm: Params, newton=False, stress=True) -> Dict[int, Tuple[to
     _check_domain(st.x, prm)
     n = prm.n_nodes
     mp = particle_mass(st, prm)
-    if prm.transfer == TRANSFER_PIC:
+    if prm.transfer in (TRANSFER_PIC, TRANSFER_APIC_GRAD):
         return _p2g_pic(st, prm, mp, newton, stress)
     D = apic_D(st.x, prm)
     Dinv = torch.linalg.inv(D)
@@ -446,9 +451,12 @@ def p2g(st: State, prm: Params, newton=False, stress=True) -> Dict[int, Tuple[to
 
 
 def _p2g_pic(st: State, prm: Params, mp, newton, stress):
-    """Reading R16: m_i = sum w m_p, m_i v_i + dt f_i = sum w m_p v_p - dt sum V0 tau grad w."""
+    """Reading R16: m_i = sum w m_p, m_i v_i + dt f_i = sum w m_p v_p - dt sum V0 tau grad w;
+    reading R17 adds the APIC term w m_p B D^-1 (x_i - x_p) to the momentum."""
     n = prm.n_nodes
     tau = kirchhoff_stress(st, prm, newton) if stress else torch.zeros_like(st.F)
+    if prm.transfer == TRANSFER_APIC_GRAD:
+        A = (mp[:, None, None] * st.B) @ torch.linalg.inv(apic_D(st.x, prm))
     out = {}
     for k in grid_ids(prm.kernel):
         idx, w, d, g = stencil_grad(st.x, prm.dx, prm.kernel, k)
@@ -456,6 +464,8 @@ def _p2g_pic(st: State, prm: Params, mp, newton, stress):
         m_contrib = (w * mp[:, None]).reshape(-1)
         p_contrib = (w[..., None] * mp[:, None, None] * st.v[:, None, :]
                      - prm.dt * prm.V0 * torch.einsum("nab,nsb->nsa", tau, g))
+        if prm.transfer == TRANSFER_APIC_GRAD:
+            p_contrib = p_contrib + w[..., None] * torch.einsum("nab,nsb->nsa", A, d)
         m = torch.zeros(n ** 3, dtype=F64).index_add(0, lin, m_contrib)
         p = torch.zeros(n ** 3, 3, dtype=F64).index_add(0, lin, p_contrib.reshape(-1, 3))
         out[k] = (m, p)
@@ -498,14 +508,14 @@ def g2p(st: State, vgrid, prm: Params):
         B = B + torch.einsum("ns,nsa,nsb->nab", w, vi, d)
     v = v / len(ks)
     B = B / len(ks)
-    if prm.transfer == TRANSFER_PIC:
-        # reading R16: grad v = 1/2 sum_k sum_i v~_i grad w_ip^T, and B = 0
+    if prm.transfer in (TRANSFER_PIC, TRANSFER_APIC_GRAD):
+        # readings R16, R17: grad v = 1/2 sum_k sum_i v~_i grad w_ip^T; PIC keeps B = 0
         C = torch.zeros(N, 3, 3, dtype=F64)
         for k in ks:
             idx, _, _, g = stencil_grad(st.x, prm.dx, prm.kernel, k)
             vi = vgrid[k][_lin(idx, n)]
             C = C + torch.einsum("nsa,nsb->nab", vi, g)
-        return v, torch.zeros_like(B), C / len(ks)
+        return v, (torch.zeros_like(B) if prm.transfer == TRANSFER_PIC else B), C / len(ks)
     Dinv = torch.linalg.inv(apic_D(st.x, prm))
     return v, B, B @ Dinv
 

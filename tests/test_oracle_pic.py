@@ -8,6 +8,13 @@ on the dual grid, = I on the single quadratic grid), exact reproduction of an
 affine grid velocity (v and grad v), linear momentum conservation of P2G with
 stress, and the P2G force equal to minus twice the gradient of the stored
 energy of F^ = (I + grad v(x^ - x)) F built by the PIC G2P itself.
+
+The APIC transfer with the kernel gradient (reading R17: Sec. 4.4's momentum
+transfer and B, the force and grad v of Sec. 4.3) is pinned by P2G linear and
+angular momentum (sum x x m v + sum m eps:B, Supplement Thm 2.1/2.2: the
+kernel-gradient force carries no torque because sum_k sum_i (x_i - x_p)
+grad w^T = |K| I), by a full step conserving both, and by the affine field
+giving B = A D and grad v = A.
 """
 import pytest
 import torch
@@ -78,9 +85,13 @@ def test_p2g_conserves_linear_momentum_with_stress(kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_pic_force_is_minus_twice_energy_gradient(kernel):
+@pytest.mark.parametrize("transfer", [O.TRANSFER_PIC, O.TRANSFER_APIC_GRAD])
+def test_pic_force_is_minus_twice_energy_gradient(kernel, transfer):
     prm = _prm(kernel)
+    prm.transfer = transfer
     st = _state(60, 12, 13, f_scale=0.15)
+    if transfer == O.TRANSFER_APIC_GRAD:  # the B term cancels in the difference below
+        st.B = 0.3 * torch.randn(60, 3, 3, dtype=F64, generator=torch.Generator().manual_seed(3))
     st.v.zero_()
     g_s = O.p2g(st, prm)
     g_0 = O.p2g(st, prm, stress=False)
@@ -103,3 +114,54 @@ def test_pic_step_keeps_B_zero_and_momentum():
     new = O.step(st, prm, bc=False)
     assert float(new.B.abs().max()) == 0.0
     assert torch.allclose(O.particle_momentum(new, prm), O.particle_momentum(st, prm), atol=1e-13, rtol=1e-11)
+
+
+def _prm_grad(kernel, res=16, dt=1e-3, model=O.FIXED_COROTATED):
+    prm = _prm(kernel, res=res, dt=dt)
+    prm.materials = [O.Mat(model, 1e5, 0.3, 1000.0, 30.0)]
+    prm.transfer = O.TRANSFER_APIC_GRAD
+    return prm
+
+
+def _state_B(n, res, seed, **kw):
+    x, v, B, F = S.random_state(n, res, seed, **kw)
+    return O.make_state(torch.from_numpy(x), torch.from_numpy(v), torch.from_numpy(B), torch.from_numpy(F))
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_apic_grad_p2g_conserves_linear_and_angular_momentum(kernel):
+    prm = _prm_grad(kernel)
+    st = _state_B(300, 16, 41, margin_cells=4.0, f_scale=0.2)
+    grids = O.p2g(st, prm)
+    P, L = O.particle_momentum(st, prm), O.particle_angular_momentum(st, prm)
+    assert torch.allclose(O.grid_momentum(grids, prm), P, atol=1e-13 * float(P.abs().max()), rtol=0)
+    assert torch.allclose(O.grid_angular_momentum(grids, prm), L, atol=1e-12 * float(L.abs().max()), rtol=0)
+    # the B term is really there: dropping B changes the grid momentum
+    st0 = O.State(st.x, st.v, torch.zeros_like(st.B), st.F, st.mat)
+    k0 = O.grid_ids(kernel)[0]
+    assert not torch.allclose(O.p2g(st0, prm)[k0][1], grids[k0][1])
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("model", [O.FIXED_COROTATED, O.DRUCKER_PRAGER])
+def test_apic_grad_step_conserves_momentum(kernel, model):
+    prm = _prm_grad(kernel, dt=1e-4, model=model)
+    st = _state_B(400, 16, 42, margin_cells=4.0, f_scale=0.1)
+    P0, L0 = O.particle_momentum(st, prm), O.particle_angular_momentum(st, prm)
+    new = O.step(st, prm, gravity=(0.0, 0.0, 0.0), bc=False)
+    assert torch.allclose(O.particle_momentum(new, prm), P0, atol=1e-12 * float(P0.abs().max()), rtol=0)
+    assert torch.allclose(O.particle_angular_momentum(new, prm), L0, atol=1e-11 * float(L0.abs().max()), rtol=0)
+    assert float(new.B.abs().max()) > 0.0
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_apic_grad_affine_field_gives_B_and_grad_v(kernel):
+    prm = _prm_grad(kernel)
+    st = _state_B(200, 16, 43, margin_cells=4.0)
+    A = torch.tensor([[0.3, -1.2, 0.5], [0.7, 0.1, -0.4], [-0.2, 0.9, 0.6]], dtype=F64)
+    b = torch.tensor([0.5, -0.25, 1.0], dtype=F64)
+    vg = {k: b + O.grid_nodes(prm, k) @ A.T for k in O.grid_ids(kernel)}
+    v, B, C = O.g2p(st, vg, prm)
+    assert torch.allclose(v, b + st.x @ A.T, atol=1e-12, rtol=0)
+    assert torch.allclose(B, A @ O.apic_D(st.x, prm), atol=1e-12, rtol=0)
+    assert torch.allclose(C, A.expand_as(C), atol=1e-10, rtol=0)

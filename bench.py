@@ -323,22 +323,26 @@ def dam_break_lines(ck, stream_ptr, warmup, steps, sizes=(4175808, 8994048)):
     return out
 
 
-def pic_lines(ck, scene, stream_ptr, warmup, steps):
-    """The PIC transfer (Sec. 4.3 with the kernel gradient) on the headline
-    scene and window: CK and quadratic ms per step, device-resident, no
+def transfer_lines(ck, scene, stream_ptr, warmup, steps):
+    """The kernel-gradient transfers on the headline scene and window: PIC
+    (Sec. 4.3) and APIC with the kernel gradient (Sec. 4.4 with the force and
+    grad v of Sec. 4.3); CK and quadratic ms per step, device-resident, no
     per-kernel events."""
-    row = {}
-    for name, kernel in (("ck", ck.KERNEL_CK), ("quadratic", ck.KERNEL_QUADRATIC)):
-        ctx, keep = _make_ctx(ck, scene, kernel | ck.TRANSFER_PIC, stream_ptr)
-        ck.ckmpm_step(ctx, warmup)
-        ck.ckmpm_sync(ctx)
-        ms = _time_steps(ck, ctx, steps, stream_ptr)
-        ck.ckmpm_sync(ctx)
-        ck.ckmpm_destroy(ctx)
-        row[name] = {"ms_per_step": ms / steps, "value": scene.n * steps / (ms / 1e3)}
-    row["ck_speedup"] = row["quadratic"]["ms_per_step"] / row["ck"]["ms_per_step"]
-    row["workload"] = f"{WORKLOAD}, PIC transfer, steps {warmup}..{warmup + steps}"
-    return row
+    out = {}
+    for tname, flag in (("pic", ck.TRANSFER_PIC), ("apic_grad", ck.TRANSFER_APIC_GRAD)):
+        row = {}
+        for name, kernel in (("ck", ck.KERNEL_CK), ("quadratic", ck.KERNEL_QUADRATIC)):
+            ctx, keep = _make_ctx(ck, scene, kernel | flag, stream_ptr)
+            ck.ckmpm_step(ctx, warmup)
+            ck.ckmpm_sync(ctx)
+            ms = _time_steps(ck, ctx, steps, stream_ptr)
+            ck.ckmpm_sync(ctx)
+            ck.ckmpm_destroy(ctx)
+            row[name] = {"ms_per_step": ms / steps, "value": scene.n * steps / (ms / 1e3)}
+        row["ck_speedup"] = row["quadratic"]["ms_per_step"] / row["ck"]["ms_per_step"]
+        out[tname] = row
+    out["workload"] = f"{WORKLOAD}, steps {warmup}..{warmup + steps}"
+    return out
 
 
 def run_gpu(args):
@@ -446,7 +450,7 @@ def run_gpu(args):
 
     served = served_mix(ck, stream_ptr) if not args.no_served else None
     dam = dam_break_lines(ck, stream_ptr, args.warmup, args.steps) if not args.no_dam else None
-    pic = pic_lines(ck, scene, stream_ptr, args.warmup, args.steps) if not args.no_pic else None
+    transfers = transfer_lines(ck, scene, stream_ptr, args.warmup, args.steps) if not args.no_transfers else None
     cb = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:
@@ -461,7 +465,7 @@ def run_gpu(args):
                                     f"the keep from about step 73)",
                            "per_kernel_ms": "second run over the same steps with CUDA events around each launch"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "quadratic": quad, "served": served, "dam_break": dam, "pic": pic}
+                "clocks": clocks, "quadratic": quad, "served": served, "dam_break": dam, "transfers": transfers}
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -481,7 +485,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-dam", action="store_true", help="skip the dam-break lines")
-    ap.add_argument("--no-pic", action="store_true", help="skip the PIC-transfer lines")
+    ap.add_argument("--no-transfers", action="store_true", help="skip the kernel-gradient transfer lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -57,8 +57,8 @@ typedef enum {
 
 typedef enum { CKMPM_KERNEL_CK = 0, CKMPM_KERNEL_QUADRATIC = 1 } ckmpm_kernel;
 
-/* Transfer scheme, OR-ed into a kernel argument (ckmpm_create, ckmpm_config,
- * ckmpm_p2g_grids_static); fixed for a context.
+/* Transfer scheme, OR-ed into a kernel argument (ckmpm_create, ckmpm_config;
+ * ckmpm_p2g_grids_static takes APIC_MLS and PIC); fixed for a context.
  *   CKMPM_TRANSFER_APIC_MLS (0, the default): APIC momentum with the MLS
  *     force, state B (Sec. 4.4, 4.5).
  *   CKMPM_TRANSFER_PIC: the PIC scheme of Sec. 4.3 with the kernel gradient
@@ -66,8 +66,17 @@ typedef enum { CKMPM_KERNEL_CK = 0, CKMPM_KERNEL_QUADRATIC = 1 } ckmpm_kernel;
  *     momentum; G2P gives v_p = 1/2 sum_k sum_i w v~_i and
  *     grad v_p = 1/2 sum_k sum_i v~_i (grad w_ip)^T for F <- (I + dt grad v) F.
  *     The state keeps no B: readback of B and C gives zeros and uploading B
- *     is EINVAL. */
-typedef enum { CKMPM_TRANSFER_APIC_MLS = 0, CKMPM_TRANSFER_PIC = 2 } ckmpm_transfer;
+ *     is EINVAL.
+ *   CKMPM_TRANSFER_APIC_GRAD: APIC with the kernel gradient (Sec. 4.4 taken
+ *     literally, "the rest as in the PIC scheme"): P2G adds
+ *     w m (v + B D^-1 (x_i - x_p)) - dt V0 tau grad w; G2P gives v and B as for
+ *     APIC and grad v as for PIC.  The state keeps B and the stress term
+ *     separately (36 more bytes per particle per pool buffer). */
+typedef enum {
+  CKMPM_TRANSFER_APIC_MLS = 0,
+  CKMPM_TRANSFER_PIC = 2,
+  CKMPM_TRANSFER_APIC_GRAD = 4
+} ckmpm_transfer;
 typedef enum { CKMPM_FIXED_COROTATED = 0, CKMPM_DRUCKER_PRAGER = 1, CKMPM_J_FLUID = 2 } ckmpm_model;
 
 /* Constitutive parameters of one material.  Lame parameters are

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libckmpm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ENONFINITE, ETIMEOUT, EBUSY, ENOTFOUND = range(9)
 KERNEL_CK, KERNEL_QUADRATIC = 0, 1
-TRANSFER_APIC_MLS, TRANSFER_PIC = 0, 2  # OR-ed into a kernel argument
+TRANSFER_APIC_MLS, TRANSFER_PIC, TRANSFER_APIC_GRAD = 0, 2, 4  # OR-ed into a kernel argument
 FIXED_COROTATED, DRUCKER_PRAGER, J_FLUID = 0, 1, 2
 FIELD_X, FIELD_V, FIELD_B, FIELD_C, FIELD_F, FIELD_E = 0, 1, 2, 3, 4, 5
 FIELD_GRID_M, FIELD_GRID_P, FIELD_GRID_V = 16, 17, 18
@@ -286,9 +286,10 @@ _FIELD_SHAPE = {FIELD_X: (3,), FIELD_V: (3,), FIELD_B: (3, 3), FIELD_C: (3, 3), 
 
 
 def kernel_code(scene) -> int:
-    """The C ABI's kernel argument for a scene: its kernel, with
-    TRANSFER_PIC when the scene asks for the PIC transfer (scene.transfer 1)."""
-    return int(scene.kernel) | (TRANSFER_PIC if getattr(scene, "transfer", 0) == 1 else 0)
+    """The C ABI's kernel argument for a scene: its kernel, with the transfer
+    flag of scene.transfer (0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient)."""
+    flag = {0: TRANSFER_APIC_MLS, 1: TRANSFER_PIC, 2: TRANSFER_APIC_GRAD}[int(getattr(scene, "transfer", 0))]
+    return int(scene.kernel) | flag
 
 
 class Simulation:

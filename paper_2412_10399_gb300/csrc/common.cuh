@@ -71,6 +71,12 @@ struct Pool {
   float* F2;
   uint32_t* ID;
   float* E;  // optional per-particle Young's modulus (may be null)
+  // APIC with the kernel gradient only (else null): T = -dt V0 tau, row-major
+  // in T0 (T00, T01, T02, T10), T1 (T11, T12, T20, T21), T2 T22; VM then
+  // holds m B without the stress
+  float4* T0;
+  float4* T1;
+  float* T2;
 };
 
 // Everything the per-step kernels read; passed by value.

@@ -84,7 +84,7 @@ struct PendingFree {
 
 struct ckmpm_ctx {
   int kind = 0;      // 0 CK, 1 quadratic
-  bool pic = false;  // PIC transfer
+  int transfer = 0;  // ckmpm_transfer
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   ckmpm_allocator alloc{};
@@ -194,6 +194,10 @@ bool alloc_pool(ckmpm_ctx* ctx, Pool& P, int64_t n) {
   bool ok = alloc_n(ctx, P.X, n) && alloc_n(ctx, P.VM0, n) && alloc_n(ctx, P.VM1, n) && alloc_n(ctx, P.VM2, n) &&
             alloc_n(ctx, P.F0, n) && alloc_n(ctx, P.F1, n) && alloc_n(ctx, P.F2, n) && alloc_n(ctx, P.ID, n);
   if (ok && ctx->per_E) ok = alloc_n(ctx, P.E, n);
+  P.T0 = P.T1 = nullptr;
+  P.T2 = nullptr;
+  if (ok && ctx->transfer == CKMPM_TRANSFER_APIC_GRAD)
+    ok = alloc_n(ctx, P.T0, n) && alloc_n(ctx, P.T1, n) && alloc_n(ctx, P.T2, n);
   return ok;
 }
 
@@ -391,10 +395,11 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
 }
 
 ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
-  if (cfg->kernel < 0 || cfg->kernel > 3)
-    return fail(ctx, CKMPM_EINVAL, "kernel must be 0 (CK) or 1 (quadratic), optionally | CKMPM_TRANSFER_PIC");
+  if (cfg->kernel < 0 || cfg->kernel > 5)
+    return fail(ctx, CKMPM_EINVAL,
+                "kernel must be 0 (CK) or 1 (quadratic), optionally | CKMPM_TRANSFER_PIC or CKMPM_TRANSFER_APIC_GRAD");
   ctx->kind = cfg->kernel & 1;
-  ctx->pic = (cfg->kernel & CKMPM_TRANSFER_PIC) != 0;
+  ctx->transfer = cfg->kernel & 6;
   if (cfg->max_particles < 1 || cfg->max_keys < 1 || cfg->max_grid_blocks < 1 || cfg->max_virtual_blocks < 1 ||
       cfg->max_scenes < 1 ||
       cfg->max_scenes > 1024 || cfg->max_materials < 1 || cfg->max_materials > 65535)
@@ -414,7 +419,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   ctx->lc.persistent_ctas = ctx->sm_count * per_sm;
   ctx->lc.sm_count = ctx->sm_count;
   ctx->lc.g2p_minb = ctx->kind == 0 ? 5 : 4;
-  ctx->lc.pic = ctx->pic;
+  ctx->lc.transfer = ctx->transfer == CKMPM_TRANSFER_PIC ? 1 : ctx->transfer == CKMPM_TRANSFER_APIC_GRAD ? 2 : 0;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
@@ -866,7 +871,7 @@ ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, 
       if (tmp) dev_free(ctx, tmp);
       return fail(ctx, CKMPM_EINVAL, "scene has no particles in the pool");
     }
-    ck::launch_read_particles(ctx->kind, ctx->pic, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id,
+    ck::launch_read_particles(ctx->kind, ctx->transfer == CKMPM_TRANSFER_PIC, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id,
                               (uint32_t)sg->start, (uint32_t)sg->n, field, out);
   }
   cudaError_t e = cudaGetLastError();
@@ -887,7 +892,7 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
         field == CKMPM_FIELD_E))
     return fail(ctx, CKMPM_EINVAL, "field cannot be uploaded");
   if (field == CKMPM_FIELD_E && !ctx->per_E) return fail(ctx, CKMPM_EINVAL, "context has no per-particle E");
-  if (field == CKMPM_FIELD_B && ctx->pic) return fail(ctx, CKMPM_EINVAL, "the PIC transfer keeps no B");
+  if (field == CKMPM_FIELD_B && ctx->transfer == CKMPM_TRANSFER_PIC) return fail(ctx, CKMPM_EINVAL, "the PIC transfer keeps no B");
   const SceneHost& h = ctx->scenes[scene_id];
   size_t want = sizeof(float) * (size_t)(field_floats(field) * h.n);
   if (bytes != want) return fail(ctx, CKMPM_EINVAL, "upload size mismatch: expected " + std::to_string(want));
@@ -901,7 +906,7 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
     CK_TRY(cudaMemcpyAsync(tmp, src, want, cudaMemcpyHostToDevice, ctx->stream), "upload copy");
     in = (const float*)tmp;
   }
-  ck::launch_write_particles(ctx->pic, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id, (uint32_t)sg->start,
+  ck::launch_write_particles(ctx->transfer == CKMPM_TRANSFER_PIC, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id, (uint32_t)sg->start,
                              (uint32_t)sg->n, field, in);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

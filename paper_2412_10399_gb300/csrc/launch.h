@@ -13,7 +13,7 @@ struct LaunchCfg {
   int persistent_ctas;  // CTAs of the persistent P2G / update / G2P launches
   int sm_count = 1;     // SMs of the device (grid of the float64 pass)
   int g2p_minb = 4;     // resident G2P warps per SM / 4 the register budget targets
-  bool pic = false;     // PIC transfer (kernel gradient) instead of APIC + MLS
+  int transfer = 0;     // 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient
 };
 
 enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4 };

@@ -90,7 +90,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
                                                         const float* F, float* grid_m, float* grid_p,
                                                         void* stream) {
   if (!sc || !sc->x || !grid_m || !grid_p) return CKMPM_EINVAL;
-  if (kernel < 0 || kernel > 3) return CKMPM_EINVAL;
+  if (kernel < 0 || kernel > 3) return CKMPM_EINVAL;  // APIC with the kernel gradient is not offered here
   const bool pic = (kernel & CKMPM_TRANSFER_PIC) != 0;
   if (pic && B) return CKMPM_EINVAL;  // the PIC transfer keeps no B
   kernel &= 1;
@@ -248,7 +248,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   ck::launch_bin(st, v, bs, ck::LB_SCATTER, (uint32_t)nvb, grid_ctas);
   ck::launch_bin(st, v, bs, ck::LB_GLIST, (uint32_t)nvb, grid_ctas);
   ck::LaunchCfg lc{st, sms * 8};
-  lc.pic = pic;
+  lc.transfer = pic ? 1 : 0;
   ck::launch_transfer(kernel, lc, v, ck::LK_P2G);
   ck::launch_read_grid(kernel, st, v, 0, 0, grid_m);
   ck::launch_read_grid(kernel, st, v, 0, 1, grid_p);

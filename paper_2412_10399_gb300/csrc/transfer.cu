@@ -284,10 +284,11 @@ __device__ __forceinline__ void for_nodes(const Sten<1>& st, Fn&& fn) {
     }
 }
 
-// PIC transfer: visit every (node, weight, kernel-derivative products) of a
-// stencil, fn(staged_index, w, gx, gy, gz) with w = Kx Ky Kz and
-// g = (K'x Ky Kz, Kx K'y Kz, Kx Ky K'z), so that grad w = -g / dx (the
-// gradient with respect to the particle position).  Needs set_grad().
+// Kernel-gradient transfers: visit every (node, weight, kernel-derivative
+// products, offsets) of a stencil, fn(staged_index, w, gx, gy, gz, dx, dy, dz)
+// with w = Kx Ky Kz and g = (K'x Ky Kz, Kx K'y Kz, Kx Ky K'z), so that
+// grad w = -g / dx (the gradient with respect to the particle position), and
+// d the node offset in cells.  Needs set_grad().
 template <typename Fn>
 __device__ __forceinline__ void for_nodes_grad(const Sten<0>& st, Fn&& fn) {
 #pragma unroll
@@ -305,7 +306,8 @@ __device__ __forceinline__ void for_nodes_grad(const Sten<0>& st, Fn&& fn) {
 #pragma unroll
         for (int sx = 0; sx < 2; ++sx) {
           const float wx = st.w[slot][0][sx];
-          fn(row + sx, wx * wyz, st.k[slot][0][sx] * wyz, wx * kyz, wx * ykz);
+          fn(row + sx, wx * wyz, st.k[slot][0][sx] * wyz, wx * kyz, wx * ykz, st.d[slot][0][sx], st.d[slot][1][sy],
+             st.d[slot][2][sz]);
         }
       }
   }
@@ -324,7 +326,7 @@ __device__ __forceinline__ void for_nodes_grad(const Sten<1>& st, Fn&& fn) {
 #pragma unroll
       for (int sx = 0; sx < 3; ++sx) {
         const float wx = st.w[0][sx];
-        fn(row + sx, wx * wyz, st.k[0][sx] * wyz, wx * kyz, wx * ykz);
+        fn(row + sx, wx * wyz, st.k[0][sx] * wyz, wx * kyz, wx * ykz, st.d[0][sx], st.d[1][sy], st.d[2][sz]);
       }
     }
 }
@@ -568,7 +570,8 @@ struct P2GBound<1> {
 // same bound with wd * dinv replaced by the largest |g_a| of for_nodes_grad:
 // CK 2 (|K1'| <= 2, at |x| = 1/2, times weights <= 1), quadratic 0.5625
 // (|N'| <= 1 times 0.75^2); both are below wd * dinv (4.04 and 0.5644), so
-// one bound serves both transfers.
+// one bound serves every transfer.  APIC with the kernel gradient keeps m B
+// and T = -dt V0 tau apart and passes |m B| + |T| (elementwise) as M.
 // The particle's two bounds (mass, momentum) go into its block's entry of
 // the per-key bound table when it is binned (G2P for the next step, admission
 // and re-keying otherwise), so P2G reads a block's bounds without a pass over
@@ -629,7 +632,7 @@ __device__ __forceinline__ void p2g_scatter_pic(const SceneDev& s, const MatDev*
   const float mass = mats[__float_as_uint(q.X.w)].mass;
   const float ms = mass * Sm;
   const float px = mass * q.a.x * Sp, py = mass * q.a.y * Sp, pz = mass * q.a.z * Sp;
-  for_nodes_grad(st, [&](int j, float w, float gx, float gy, float gz) {
+  for_nodes_grad(st, [&](int j, float w, float gx, float gy, float gz, float, float, float) {
     atomicAdd(&sm[0][j], __float2int_rn(w * ms));
     atomicAdd(&sm[1][j], __float2int_rn(fmaf(w, px, A[0] * gx + A[1] * gy + A[2] * gz)));
     atomicAdd(&sm[2][j], __float2int_rn(fmaf(w, py, A[3] * gx + A[4] * gy + A[5] * gz)));
@@ -637,13 +640,50 @@ __device__ __forceinline__ void p2g_scatter_pic(const SceneDev& s, const MatDev*
   });
 }
 
-template <int KIND, bool PIC>
+// APIC with the kernel gradient: M = m B (state), T = -dt V0 tau (separate
+// arrays); a node receives w (m v + A d) + G g with A = m B D^-1 / dx (the
+// APIC momentum) and G = -T / dx (the force), both pre-scaled.
+template <int KIND>
+__device__ __forceinline__ void p2g_scatter_grad(const SceneDev& s, const MatDev* mats, uint32_t* err,
+                                                 const P2GPart& q, const float* T, int ox, int oy, int oz, float Sm,
+                                                 float Sp, int (*sm)[Geo<KIND>::NS]) {
+  Sten<KIND> st;
+  if (!st.set(q.X.x * s.inv_dx, q.X.y * s.inv_dx, q.X.z * s.inv_dx, ox, oy, oz)) {
+    flag_error(err, CK_ERR_INTERNAL);
+    return;
+  }
+  st.set_grad();
+  const float M[9] = {q.a.w, q.b.x, q.b.y, q.b.z, q.b.w, q.c.x, q.c.y, q.c.z, q.c.w};
+  float A[9], G[9];
+  mul_dinv(st, M, s.inv_dx * Sp, A);
+  const float sc = -s.inv_dx * Sp;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) G[r] = sc * T[r];
+  const float mass = mats[__float_as_uint(q.X.w)].mass;
+  const float ms = mass * Sm;
+  const float px = mass * q.a.x * Sp, py = mass * q.a.y * Sp, pz = mass * q.a.z * Sp;
+  for_nodes_grad(st, [&](int j, float w, float gx, float gy, float gz, float dx, float dy, float dz) {
+    atomicAdd(&sm[0][j], __float2int_rn(w * ms));
+    atomicAdd(&sm[1][j], __float2int_rn(fmaf(w, px + A[0] * dx + A[1] * dy + A[2] * dz,
+                                             G[0] * gx + G[1] * gy + G[2] * gz)));
+    atomicAdd(&sm[2][j], __float2int_rn(fmaf(w, py + A[3] * dx + A[4] * dy + A[5] * dz,
+                                             G[3] * gx + G[4] * gy + G[5] * gz)));
+    atomicAdd(&sm[3][j], __float2int_rn(fmaf(w, pz + A[6] * dx + A[7] * dy + A[8] * dz,
+                                             G[6] * gx + G[7] * gy + G[8] * gz)));
+  });
+}
+
+// TR: transfer, 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient.
+template <int KIND, int TR>
 __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   constexpr uint32_t CAP = kP2GStage, C = kP2GStage / 32;
   static_assert(C % 2 == 1, "lane stride must be odd");
   __shared__ __align__(16) int sm[4][NS];
   __shared__ float4 sX[CAP], sA[CAP], sB[CAP], sC[CAP];
+  constexpr uint32_t TCAP = TR == 2 ? CAP : 1;  // the stress term T (kernel-gradient APIC only)
+  __shared__ float4 sT0[TCAP], sT1[TCAP];
+  __shared__ float sT2[TCAP];
   __shared__ uint32_t bslot[8];
   const uint32_t npb = *v.n_pb;
   const uint32_t lane = threadIdx.x;
@@ -679,6 +719,11 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
           cp_async16(&sA[i], &v.cur.VM0[p]);
           cp_async16(&sB[i], &v.cur.VM1[p]);
           cp_async16(&sC[i], &v.cur.VM2[p]);
+          if constexpr (TR == 2) {
+            cp_async16(&sT0[i], &v.cur.T0[p]);
+            cp_async16(&sT1[i], &v.cur.T1[p]);
+            cp_async4(&sT2[i], &v.cur.T2[p]);
+          }
         }
       }
       cp_async_wait_all();
@@ -688,10 +733,15 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
         const uint32_t i = lane * C + r;
         if (i < m) {
           const P2GPart q{sX[i], sA[i], sB[i], sC[i]};
-          if constexpr (PIC)
+          if constexpr (TR == 1) {
             p2g_scatter_pic<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
-          else
+          } else if constexpr (TR == 2) {
+            const float4 t0 = sT0[i], t1 = sT1[i];
+            const float T[9] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, sT2[i]};
+            p2g_scatter_grad<KIND>(s, v.mats, v.err, q, T, ox, oy, oz, Sm, Sp, sm);
+          } else {
             p2g_scatter<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
+          }
         }
       }
       __syncwarp();  // the next chunk overwrites the staged copies
@@ -767,7 +817,8 @@ __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(
 constexpr int kG2PWarp = 32;
 __host__ __device__ constexpr int g2p_stage(int minb) { return minb >= 5 ? 64 : 128; }  // particles per chunk
 
-template <int KIND, int MINB, bool PIC>
+// TR: transfer, 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient.
+template <int KIND, int MINB, int TR>
 __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
   constexpr int CAP = g2p_stage(MINB);
@@ -841,13 +892,22 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
         continue;
       }
       float vel[3], Bh[9], G[9];
-      if constexpr (PIC) {
+      if constexpr (TR == 1) {
         // grad v = -Gr / dx (Gr in Bh); F' = (I + dt grad v) F
         st.set_grad();
         g2p_gather_grad(st, sv, vel, Bh);
         const float sc = -s.dt * s.inv_dx;
 #pragma unroll
         for (int q = 0; q < 9; ++q) G[q] = sc * Bh[q];
+      } else if constexpr (TR == 2) {
+        // B from the APIC moments, grad v = -Gr / dx from the derivative sums
+        g2p_gather(st, sv, vel, Bh);
+        st.set_grad();
+        float vg[3];
+        g2p_gather_grad(st, sv, vg, G);
+        const float sc = -s.dt * s.inv_dx;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) G[q] *= sc;
       } else {
         // C = B D^-1 = Bh D^-1 / dx ; F' = (I + dt C) F
         g2p_gather(st, sv, vel, Bh);
@@ -909,18 +969,20 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
           constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, U, e, sg);
         }
       }
-      // M' = m B' - dt V0 tau, B' = dx Bh (APIC) or 0 (PIC)
+      // M' = m B' - dt V0 tau, B' = dx Bh (APIC) or 0 (PIC); the kernel-
+      // gradient APIC keeps M' = m B' and T' = -dt V0 tau apart
       const float mdx = mt.mass * s.dx, dtv = s.dt * s.V0;
       float Mn[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Mn[q] = PIC ? -dtv * tau[q] : mdx * Bh[q] - dtv * tau[q];
+      for (int q = 0; q < 9; ++q)
+        Mn[q] = TR == 1 ? -dtv * tau[q] : TR == 2 ? mdx * Bh[q] : mdx * Bh[q] - dtv * tau[q];
       float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
       // next key; particles leaving the interior are clamped and flagged
       float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
       // x was finite, so x + dt v is finite when v is
       bool fin = isfinite(vx) && isfinite(vy) && isfinite(vz);
 #pragma unroll
-      for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]);
+      for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]) && (TR != 2 || isfinite(tau[q]));
       if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
       if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {
         flag_error(v.err, CK_ERR_DOMAIN);
@@ -947,7 +1009,20 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       if (v.nxt.E) v.nxt.E[t] = Ep;
       v.key_nxt[t] = nk;
       float bmass, bmom;
-      p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mn, bmass, bmom);
+      if constexpr (TR == 2) {
+        float Tn[9], Mb[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          Tn[q] = -dtv * tau[q];
+          Mb[q] = fabsf(Mn[q]) + fabsf(Tn[q]);
+        }
+        v.nxt.T0[t] = make_float4(Tn[0], Tn[1], Tn[2], Tn[3]);
+        v.nxt.T1[t] = make_float4(Tn[4], Tn[5], Tn[6], Tn[7]);
+        v.nxt.T2[t] = Tn[8];
+        p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mb, bmass, bmom);
+      } else {
+        p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mn, bmass, bmom);
+      }
       warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, nk, bmass, bmom);
     }
     __syncwarp();  // the next chunk (or block) overwrites the staged copies
@@ -962,7 +1037,8 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
 // degenerate, inverted or flagged by the scene's criteria) get the full
 // rotation-variant SVD and constitutive update in float64.  G2P stored the
 // advanced F' and M = m B'; this pass stores the projected F, subtracts
-// dt V0 tau from M and raises the particle's block bounds to cover the new M.
+// dt V0 tau from M (with the kernel-gradient APIC: stores T = -dt V0 tau) and
+// raises the particle's block bounds to cover the new M.
 // Grid-stride over the list; an empty list returns at once.
 template <int KIND>
 __global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
@@ -984,14 +1060,26 @@ __global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
     constitutive<double>(mt.model, F, mu, lam, (double)mt.alpha, tau, sg);
     const double dtv = (double)s.dt * (double)s.V0;
     float4 a = v.nxt.VM0[t], b = v.nxt.VM1[t], c = v.nxt.VM2[t];
-    a.w = (float)(a.w - dtv * tau[0]);
-    b = make_float4((float)(b.x - dtv * tau[1]), (float)(b.y - dtv * tau[2]), (float)(b.z - dtv * tau[3]),
-                    (float)(b.w - dtv * tau[4]));
-    c = make_float4((float)(c.x - dtv * tau[5]), (float)(c.y - dtv * tau[6]), (float)(c.z - dtv * tau[7]),
-                    (float)(c.w - dtv * tau[8]));
+    float Tn[9];
+    const bool sep = v.nxt.T0 != nullptr;  // stress term kept apart from m B
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Tn[q] = (float)(-dtv * tau[q]);
+    if (sep) {
+      v.nxt.T0[t] = make_float4(Tn[0], Tn[1], Tn[2], Tn[3]);
+      v.nxt.T1[t] = make_float4(Tn[4], Tn[5], Tn[6], Tn[7]);
+      v.nxt.T2[t] = Tn[8];
+    } else {
+      a.w = (float)(a.w - dtv * tau[0]);
+      b = make_float4((float)(b.x - dtv * tau[1]), (float)(b.y - dtv * tau[2]), (float)(b.z - dtv * tau[3]),
+                      (float)(b.w - dtv * tau[4]));
+      c = make_float4((float)(c.x - dtv * tau[5]), (float)(c.y - dtv * tau[6]), (float)(c.z - dtv * tau[7]),
+                      (float)(c.w - dtv * tau[8]));
+    }
     float Ff[9];
     bool fin = isfinite(a.w) && isfinite(b.x) && isfinite(b.y) && isfinite(b.z) && isfinite(b.w) &&
                isfinite(c.x) && isfinite(c.y) && isfinite(c.z) && isfinite(c.w);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) fin = fin && isfinite(Tn[q]);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       Ff[q] = (float)F[q];
@@ -1004,7 +1092,11 @@ __global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
     v.nxt.F0[t] = make_float4(Ff[0], Ff[1], Ff[2], Ff[3]);
     v.nxt.F1[t] = make_float4(Ff[4], Ff[5], Ff[6], Ff[7]);
     v.nxt.F2[t] = Ff[8];
-    const float Mn[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    float Mn[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    if (sep) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Mn[q] = fabsf(Mn[q]) + fabsf(Tn[q]);
+    }
     float bmass, bmom;
     p2g_bounds<KIND>(s.inv_dx, mt.mass, a.x, a.y, a.z, Mn, bmass, bmom);
     const uint32_t nk = v.key_nxt[t];
@@ -1065,11 +1157,17 @@ __device__ __forceinline__ void lame_of(const MatDev& mt, const Pool& P, uint32_
   }
 }
 
-// B = (M + dt V0 tau(F)) / m
+// B = (M + dt V0 tau(F)) / m; with the stress term kept apart, B = M / m
 __device__ __forceinline__ void recover_B(const Pool& P, const SceneDev& s, const MatDev& mt, uint32_t t, float* B) {
   float F[9], M[9], tau[9];
-  load_F(P, t, F);
   load_M(P, t, M);
+  if (P.T0) {
+    const float im = 1.0f / mt.mass;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) B[q] = M[q] * im;
+    return;
+  }
+  load_F(P, t, F);
   float mu, lam;
   lame_of(mt, P, t, mu, lam);
   stress_of(mt, F, mu, lam, tau);
@@ -1141,7 +1239,7 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
       load_F(P, t, F);
       lame_of(mt, P, t, mu, lam);
       stress_of(mt, F, mu, lam, tau);
-      for (int q = 0; q < 9; ++q) M[q] = mt.mass * in[9 * id + q] - dtv * tau[q];
+      for (int q = 0; q < 9; ++q) M[q] = mt.mass * in[9 * id + q] - (P.T0 ? 0.f : dtv * tau[q]);
       store_M(P, t, M);
     } else if (field == 4 || field == 5) {
       float B[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1157,8 +1255,14 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
       load_F(P, t, F);
       lame_of(mt, P, t, mu, lam);
       stress_of(mt, F, mu, lam, tau);
-      for (int q = 0; q < 9; ++q) M[q] = mt.mass * B[q] - dtv * tau[q];
-      store_M(P, t, M);
+      if (P.T0) {  // m B stays; the stress term follows the new F (or E)
+        P.T0[t] = make_float4(-dtv * tau[0], -dtv * tau[1], -dtv * tau[2], -dtv * tau[3]);
+        P.T1[t] = make_float4(-dtv * tau[4], -dtv * tau[5], -dtv * tau[6], -dtv * tau[7]);
+        P.T2[t] = -dtv * tau[8];
+      } else {
+        for (int q = 0; q < 9; ++q) M[q] = mt.mass * B[q] - dtv * tau[q];
+        store_M(P, t, M);
+      }
     }
   }
 }
@@ -1237,6 +1341,11 @@ __global__ void k_admit(Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd, con
     P.F2[t] = 1.f;
     P.ID[t] = i;
     if (P.E) P.E[t] = E ? E[i] : 0.f;
+    if (P.T0) {  // tau(I) = 0 for every model
+      P.T0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      P.T1[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      P.T2[t] = 0.f;
+    }
     uint32_t k = particle_key<KIND>(s, ux, uy, uz);
     key[t] = k;
     const float M0[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1275,7 +1384,12 @@ __global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd, con
     uint32_t k = particle_key<KIND>(s, ux, uy, uz);
     key[t] = k;
     const float4 a = P.VM0[t], b = P.VM1[t], c = P.VM2[t];
-    const float M[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    float M[9] = {a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    if (P.T0) {
+      const float4 t0 = P.T0[t], t1 = P.T1[t];
+      const float T[9] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, P.T2[t]};
+      for (int q = 0; q < 9; ++q) M[q] = fabsf(M[q]) + fabsf(T[q]);
+    }
     float bmass, bmom;
     p2g_bounds<KIND>(s.inv_dx, mt.mass, a.x, a.y, a.z, M, bmass, bmom);
     warp_aggregated_bin(cnt, bnd, k, bmass, bmom);
@@ -1288,10 +1402,12 @@ template <int KIND>
 static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
     case LK_P2G:
-      if (lc.pic)
-        k_p2g<KIND, true><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+      if (lc.transfer == 1)
+        k_p2g<KIND, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+      else if (lc.transfer == 2)
+        k_p2g<KIND, 2><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       else
-        k_p2g<KIND, false><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+        k_p2g<KIND, 0><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       break;
     // a wide grid: each CTA's block loop is short, so the dependent loads of
     // one block (list entry, scene, accumulators) overlap across CTAs
@@ -1301,15 +1417,19 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
       // chunks) for the compact kernel and 16 (128 registers) for the
       // quadratic twin by default, the faster of each on the large-impact
       // scene; 24 (80 registers) on request.  One resident wave.
-      // The PIC transfer runs each kernel's default budget only.
-      if (lc.pic)
-        k_g2p<KIND, KIND == 0 ? 5 : 4, true><<<lc.sm_count * (KIND == 0 ? 20 : 16), kG2PWarp, 0, lc.stream>>>(v);
+      // The kernel-gradient transfers run one budget each: PIC the APIC
+      // default; the kernel-gradient APIC (two gathers) 16 warps/SM for CK
+      // and 12 (170 registers, no spills) for the quadratic twin.
+      if (lc.transfer == 1)
+        k_g2p<KIND, KIND == 0 ? 5 : 4, 1><<<lc.sm_count * (KIND == 0 ? 20 : 16), kG2PWarp, 0, lc.stream>>>(v);
+      else if (lc.transfer == 2)
+        k_g2p<KIND, KIND == 0 ? 4 : 3, 2><<<lc.sm_count * (KIND == 0 ? 16 : 12), kG2PWarp, 0, lc.stream>>>(v);
       else if (lc.g2p_minb >= 6)
-        k_g2p<KIND, 6, false><<<lc.sm_count * 24, kG2PWarp, 0, lc.stream>>>(v);
+        k_g2p<KIND, 6, 0><<<lc.sm_count * 24, kG2PWarp, 0, lc.stream>>>(v);
       else if (lc.g2p_minb == 5)
-        k_g2p<KIND, 5, false><<<lc.sm_count * 20, kG2PWarp, 0, lc.stream>>>(v);
+        k_g2p<KIND, 5, 0><<<lc.sm_count * 20, kG2PWarp, 0, lc.stream>>>(v);
       else
-        k_g2p<KIND, 4, false><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
+        k_g2p<KIND, 4, 0><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
       break;
     case LK_G2P_FP64: k_g2p_fp64<KIND><<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;

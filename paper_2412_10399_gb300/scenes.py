@@ -44,6 +44,7 @@ KERNEL_QUADRATIC = 1   # quadratic B-spline MLS-MPM on one grid (comparison path
 # Transfer schemes.
 TRANSFER_APIC_MLS = 0  # APIC momentum with the MLS force (Sec. 4.4, 4.5)
 TRANSFER_PIC = 1       # PIC of Sec. 4.3 with the kernel gradient
+TRANSFER_APIC_GRAD = 2  # APIC momentum (Sec. 4.4) with the kernel-gradient force and grad v
 
 
 def splitmix64(counter: np.ndarray, seed: int) -> np.ndarray:

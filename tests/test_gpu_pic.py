@@ -1,5 +1,7 @@
-"""Parity of the CUDA PIC transfer (Sec. 4.3 with the kernel gradient, the
-oracle's reading R16) with the FP64 oracle, through the C ABI.
+"""Parity of the CUDA kernel-gradient transfers with the FP64 oracle, through
+the C ABI: PIC (Sec. 4.3 with the kernel gradient, the oracle's reading R16)
+and APIC with the kernel gradient (Sec. 4.4 momentum and B, the force and
+grad v of Sec. 4.3; reading R17).
 
 Tolerances are those of the APIC parity tests: grid mass and momentum after
 P2G within 1e-5 of the largest oracle value per field and grid; one-step x
@@ -13,8 +15,9 @@ node's mass comes mostly from this particle its velocity error (unit / mass)
 enters grad v multiplied by |grad w| / w ~ 3 / (eps dx).  The sparse random
 states here (about 0.4 particles per cell, random velocities) make such nodes
 common; APIC weights the same velocity by w and has no such factor.
-The state keeps no B: B and C read back as zeros and an upload of B is
-refused.
+The PIC state keeps no B: B and C read back as zeros and an upload of B is
+refused.  The kernel-gradient APIC keeps B (within 5e-5 relative after one
+step, as for APIC + MLS) and its stress term apart.
 """
 import numpy as np
 import pytest
@@ -156,3 +159,106 @@ def test_pic_static_p2g_matches_context_path(kernel):
     ck.ckmpm_p2g_grids_static(scs, ck.kernel_code(sc), 0, Fd.data_ptr(), gm.data_ptr(), gp.data_ptr(), stream)
     assert rel(gm.cpu().numpy(), gm_ref) <= 1e-5
     assert rel(gp.cpu().numpy(), gp_ref) <= 1e-5
+
+
+# ------------------------------------------------- APIC with the kernel gradient
+
+def _grad_scene(n, res, seed, model, kernel, **kw):
+    sc, B, F = random_scene(n, res, seed, model=model, kernel=kernel, **kw)
+    sc.transfer = S.TRANSFER_APIC_GRAD
+    return sc, B, F
+
+
+def _grad_sim(ck, sc, B, F):
+    sim = ck.Simulation(sc, ck.kernel_code(sc))
+    sim.write(ck.FIELD_F, F)
+    sim.write(ck.FIELD_B, B)
+    return sim
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("n,res,seed", [(1, 16, 51), (777, 16, 52), (6000, 32, 53)])
+def test_apic_grad_p2g_grid_parity(kernel, model, n, res, seed):
+    ck = need_gpu()
+    sc, B, F = _grad_scene(n, res, seed, model, kernel, f_scale=0.08)
+    sim = _grad_sim(ck, sc, B, F)
+    sim.probe_grids()
+    gm = sim.read(ck.FIELD_GRID_M)
+    gp = sim.read(ck.FIELD_GRID_P)
+    sim.close()
+    prm = O.params_from_scene(sc)
+    assert prm.transfer == O.TRANSFER_APIC_GRAD
+    _grid_check(sc, gm, gp, O.p2g(oracle_state(sc, B, F), prm))
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_apic_grad_p2g_grid_parity_dense_blocks(kernel):
+    ck = need_gpu()
+    sc, B, F = _grad_scene(32768, 32, 54, S.DRUCKER_PRAGER, kernel, f_scale=0.08, box=(8.0, 24.0))
+    sim = _grad_sim(ck, sc, B, F)
+    sim.probe_grids()
+    gm = sim.read(ck.FIELD_GRID_M)
+    gp = sim.read(ck.FIELD_GRID_P)
+    sim.close()
+    _grid_check(sc, gm, gp, O.p2g(oracle_state(sc, B, F), O.params_from_scene(sc)))
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("model,f_scale", [(S.FIXED_COROTATED, 0.08), (S.DRUCKER_PRAGER, 0.08),
+                                           (S.DRUCKER_PRAGER, 0.008), (S.J_FLUID, 0.05)])
+def test_apic_grad_one_step_particle_parity(kernel, model, f_scale):
+    ck = need_gpu()
+    E = 1e4 if model == S.J_FLUID else 1e5
+    sc, B, F = _grad_scene(5000, 32, 55, model, kernel, f_scale=f_scale, E=E)
+    sim = _grad_sim(ck, sc, B, F)
+    sim.step(1)
+    sim.sync()
+    got = {f: sim.read(f) for f in (ck.FIELD_X, ck.FIELD_V, ck.FIELD_F, ck.FIELD_B, ck.FIELD_C)}
+    sim.close()
+    prm = O.params_from_scene(sc)
+    new = O.step(oracle_state(sc, B, F), prm)
+    assert np.abs(got[ck.FIELD_X] - new.x.numpy()).max() <= 1e-6 * sc.dx + 2e-7
+    assert rel(got[ck.FIELD_V], new.v.numpy()) <= 2e-5
+    Fo = new.F.numpy()
+    err = np.abs(got[ck.FIELD_F] - Fo).reshape(-1, 9).max(1) / np.abs(Fo).max()
+    assert np.quantile(err, 0.99) <= 2e-6 and err.max() <= 1e-5, (np.quantile(err, 0.99), err.max())
+    assert rel(got[ck.FIELD_B], new.B.numpy()) <= 5e-5
+    C = new.B @ torch.linalg.inv(O.apic_D(new.x, prm))
+    assert rel(got[ck.FIELD_C], C.numpy()) <= 1e-4
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_apic_grad_dam_break_40_steps_positions(kernel):
+    ck = need_gpu()
+    res, n = 64, 16 * 12 * 16 * 8
+    dx = 1.0 / res
+    u = S.uniform01(np.arange(3 * n, dtype=np.uint64) + np.uint64(1 << 50), 3).reshape(n, 3)
+    x = (4.0 + u * np.array([16.0, 12.0, 16.0])) * dx
+    sc = S.Scene("small_dam_break_apic_grad", res, dx, 1e-4, f32(x).astype(np.float64), np.zeros_like(x),
+                 np.zeros(n, np.uint8), [S.FLUID], kernel=kernel, transfer=S.TRANSFER_APIC_GRAD)
+    sim = ck.Simulation(sc, ck.kernel_code(sc))
+    sim.step(40)
+    sim.sync()
+    xg = sim.read(ck.FIELD_X)
+    sim.close()
+    st = O.run(O.state_from_scene(sc), O.params_from_scene(sc), 40)
+    assert np.abs(xg - st.x.numpy()).max() <= 1e-3 * dx
+
+
+def test_apic_grad_B_roundtrip_and_static_entry_refuses():
+    ck = need_gpu()
+    sc, B, F = _grad_scene(500, 16, 56, S.FIXED_COROTATED, S.KERNEL_CK, f_scale=0.08)
+    sim = _grad_sim(ck, sc, B, F)
+    assert rel(sim.read(ck.FIELD_B), B) <= 1e-6  # B = M / m, no stress round trip
+    assert rel(sim.read(ck.FIELD_F), F) == 0.0
+    sim.close()
+    scs, keep = ck.make_scene(sc.res, sc.dx, sc.dt, sc.materials, torch.from_numpy(f32(sc.x)).cuda(),
+                              torch.from_numpy(f32(sc.v)).cuda(), torch.from_numpy(sc.mat.copy()).cuda())
+    nn = sc.res + 1
+    gm = torch.zeros((2, nn, nn, nn), dtype=torch.float32, device="cuda")
+    gp = torch.zeros((2, nn, nn, nn, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(ck.CKMPMError) as e:
+        ck.ckmpm_p2g_grids_static(scs, ck.kernel_code(sc), 0, 0, gm.data_ptr(), gp.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == ck.EINVAL

@@ -23,6 +23,19 @@ BYTES_PER_PARTICLE = 2 * (16 + 48 + 16 + 16 + 4 + 4) + 2 * 4 + 4 + 4  # two pool
 BYTES_PER_KEY = 6 * 4 + 2 * 2 * 4                                  # histograms x2, offset, cursor, block list x2, P2G bounds x2
 BYTES_PER_VIRTUAL_BLOCK = 2 * 4                                    # flag, table entry
 BYTES_PER_POOL_BLOCK_CK = 2 * 2 * 64 * 16 + 2 * 4                  # Gacc + Gvel for both grids, list entries
+BYTES_PER_PARTICLE_APIC_GRAD = 2 * 36                              # the separate stress term, both pools
+
+
+def bytes_per_particle(kernel: int = 0) -> int:
+    """Device bytes per particle for a kernel argument (kernel | transfer flag):
+    APIC with the kernel gradient (flag 4) keeps its stress term in 36 more
+    bytes per pool buffer."""
+    return BYTES_PER_PARTICLE + (BYTES_PER_PARTICLE_APIC_GRAD if kernel & 4 else 0)
+
+
+def bytes_per_pool_block(kernel: int = 0) -> int:
+    """Device bytes per grid pool block: two grids for CK, one for the quadratic twin."""
+    return BYTES_PER_POOL_BLOCK_CK if (kernel & 1) == 0 else BYTES_PER_POOL_BLOCK_CK // 2 + 4
 
 
 def scene_resources(n: int, res: int) -> Dict[str, int]:
@@ -48,19 +61,24 @@ class Budget:
     scenes: int
 
     @staticmethod
-    def from_bytes(budget: int, max_res: int = 128, max_scenes: int = 64) -> "Budget":
+    def from_bytes(budget: int, max_res: int = 128, max_scenes: int = 64, kernel: int = 0) -> "Budget":
         """Split a byte budget: key space and block tables sized for max_scenes
         scenes of max_res^3; the rest shared by particles and pool blocks in the
-        ratio a compact 8-ppc scene uses them (n/64 pool blocks per particle)."""
+        ratio a compact 8-ppc scene uses them (n/64 pool blocks per particle).
+        kernel: the context's kernel argument (kernel | transfer flag)."""
         r = scene_resources(0, max_res)
         keys = r["keys"] * max_scenes
         vblocks = r["virtual_blocks"] * max_scenes
         rest = budget - keys * BYTES_PER_KEY - vblocks * BYTES_PER_VIRTUAL_BLOCK
         if rest <= 0:
             raise ValueError("budget too small for the key space and block tables")
-        per_particle = BYTES_PER_PARTICLE + BYTES_PER_POOL_BLOCK_CK / 64.0
+        pool_blocks_extra = 64 * max_scenes
+        rest -= pool_blocks_extra * bytes_per_pool_block(kernel)
+        if rest <= 0:
+            raise ValueError("budget too small for the key space and block tables")
+        per_particle = bytes_per_particle(kernel) + bytes_per_pool_block(kernel) / 64.0
         particles = int(rest // per_particle)
-        return Budget(particles, keys, vblocks, particles // 64 + 64 * max_scenes, max_scenes)
+        return Budget(particles, keys, vblocks, particles // 64 + pool_blocks_extra, max_scenes)
 
     def fits(self, used: Dict[str, int], need: Dict[str, int]) -> bool:
         cap = dataclasses.asdict(self)

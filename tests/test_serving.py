@@ -96,11 +96,13 @@ def test_oversized_request_is_refused():
         srv.submit(SV.Request(_scene("big", 100000), 1))
 
 
-def test_budget_from_bytes_stays_within_the_budget():
-    b = SV.Budget.from_bytes(8 << 30, max_res=128, max_scenes=16)
-    used = (b.particles * SV.BYTES_PER_PARTICLE + b.keys * SV.BYTES_PER_KEY
-            + b.virtual_blocks * SV.BYTES_PER_VIRTUAL_BLOCK + b.pool_blocks * SV.BYTES_PER_POOL_BLOCK_CK)
-    assert used <= (8 << 30) * 1.05
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5])
+def test_budget_from_bytes_stays_within_the_budget(kernel):
+    b = SV.Budget.from_bytes(8 << 30, max_res=128, max_scenes=16, kernel=kernel)
+    used = (b.particles * SV.bytes_per_particle(kernel) + b.keys * SV.BYTES_PER_KEY
+            + b.virtual_blocks * SV.BYTES_PER_VIRTUAL_BLOCK + b.pool_blocks * SV.bytes_per_pool_block(kernel))
+    assert used <= (8 << 30)
+    assert used >= (8 << 30) * 0.999
     assert b.particles > 10_000_000
     # every scene that fits alone fits the pool reservation
     assert b.fits({}, SV.scene_resources(2_000_000, 128))

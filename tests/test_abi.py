@@ -60,3 +60,49 @@ def test_invalid_scene_is_rejected_before_any_device_work():
     sc.res = 16
     sc.dt = -1.0
     assert ckmpm.load().ckmpm_create(ctypes.byref(sc), 0, None, ctypes.byref(out)) == ckmpm.EINVAL
+
+
+def _header_text():
+    return "\n".join(open(h).read() for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
+
+
+def _strip_comments(txt):
+    return re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+
+
+def test_binding_constants_match_the_header_enums():
+    """Every CKMPM_* enumerator of the header has the value the Python binding uses."""
+    from paper_2412_10399_gb300 import ckmpm
+    txt = _strip_comments(_header_text())
+    enums = {}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", txt, flags=re.S):
+        for name, val in re.findall(r"(CKMPM_\w+)\s*=\s*(\d+)", body):
+            enums[name] = int(val)
+    assert len(enums) >= 25
+    for name, val in enums.items():
+        py = name[len("CKMPM_"):]
+        if py.startswith("FIELD_") or py.startswith("KERNEL_") or py.startswith("TRANSFER_") or \
+                py in ckmpm.STATUS_NAMES or py in ("FIXED_COROTATED", "DRUCKER_PRAGER", "J_FLUID"):
+            assert getattr(ckmpm, py) == val, name
+
+
+def test_binding_structs_match_the_header_field_order():
+    """The ctypes structures list the header's struct members in the same order
+    (the C ABI passes them by layout)."""
+    from paper_2412_10399_gb300 import ckmpm
+    txt = _strip_comments(_header_text())
+    structs = {}
+    for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(ckmpm_\w+)\s*;", txt, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            m = re.search(r"\(\s*\*\s*(\w+)\s*\)", decl)  # function pointer
+            if m is None:
+                m = re.search(r"(\w+)\s*(\[[^\]]*\])?\s*$", decl)
+            fields.append(m.group(1))
+        structs[name] = fields
+    for name in ("ckmpm_material", "ckmpm_scene", "ckmpm_allocator", "ckmpm_config", "ckmpm_stats"):
+        py = [f[0] for f in getattr(ckmpm, name)._fields_]
+        assert py == structs[name], name

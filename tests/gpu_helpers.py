@@ -45,3 +45,23 @@ def rel(gpu, ref):
     d = np.abs(np.asarray(gpu, np.float64) - ref).max()
     s = np.abs(ref).max()
     return d / s if s > 0 else d
+
+
+def window_step(x, v, B, F, mat, cell, p, prm_local, dx, halo=3):
+    """One oracle step of particle p computed on a small local domain: every
+    particle within `halo` cells of p (all that reach p's stencil nodes)
+    shifted by a whole number of cells so that p's cell lands at the centre
+    of a prm_local.res^3 domain, stepped without walls; returns p's
+    (x, v, F, B) in the original frame and the neighbourhood's indices.
+    Exact for p as long as the original domain's walls touch none of p's
+    nodes (the shift is a multiple of dx, a power of two)."""
+    near = np.flatnonzero(np.all(np.abs(cell - cell[p]) <= halo, axis=1))
+    shift = (cell[p].astype(np.int64) - prm_local.res // 2) * dx
+    st = O.make_state(torch.from_numpy(np.asarray(x[near], np.float64) - shift),
+                      torch.from_numpy(np.asarray(v[near], np.float64)),
+                      torch.from_numpy(np.asarray(B[near], np.float64)),
+                      torch.from_numpy(np.asarray(F[near], np.float64)),
+                      mat=torch.from_numpy(np.asarray(mat[near]).astype(np.int64)))
+    new = O.step(st, prm_local, bc=False)
+    i = int(np.flatnonzero(near == p)[0])
+    return (new.x[i].numpy() + shift, new.v[i].numpy(), new.F[i].numpy(), new.B[i].numpy()), near, new, st

@@ -22,11 +22,13 @@ namespace ck {
 
 constexpr float kInv2Pi = 0.15915494309189535f;
 
-// Asynchronous global -> shared copies (cp.async, cached in L1 and L2): a CTA
-// issues the gathers of a whole particle block before it waits for any.
+// Asynchronous global -> shared copies: a CTA issues the gathers of a whole
+// chunk of particles before it waits for any.  The 16-byte copies stream
+// through L2 only (.cg), so that the particle stream does not evict the small
+// tables every particle reads through L1 (materials, scenes, block lists).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);

@@ -594,6 +594,29 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
     ctx->mat_alloc.give(mb, sc->n_materials);
     return fail(ctx, CKMPM_ENOMEM, "staging allocation failed");
   }
+  // per-particle E defaults to the material's E; its temporary is taken
+  // before the scene is recorded, so that a failure leaves nothing behind
+  float* dE = nullptr;
+  if (ctx->per_E) {
+    std::vector<float> Ehost((size_t)sc->n);
+    std::vector<uint8_t> mh;
+    if (sc->mat) {
+      mh.resize((size_t)sc->n);
+      if (sc->is_device)
+        CK_TRY(cudaMemcpy(mh.data(), sc->mat, (size_t)sc->n, cudaMemcpyDeviceToHost), "read mat");
+      else
+        std::memcpy(mh.data(), sc->mat, (size_t)sc->n);
+    }
+    for (int64_t i = 0; i < sc->n; ++i) Ehost[i] = (float)sc->materials[sc->mat ? mh[i] : 0].E;
+    dE = (float*)dev_alloc(ctx, sizeof(float) * (size_t)sc->n);
+    if (!dE) {
+      ctx->keys_alloc.give(kb, nkeys);
+      ctx->grid_alloc.give(gb, nvb);
+      ctx->mat_alloc.give(mb, sc->n_materials);
+      return fail(ctx, CKMPM_ENOMEM, "allocation failed");
+    }
+    CK_TRY(cudaMemcpyAsync(dE, Ehost.data(), sizeof(float) * sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload E");
+  }
   SceneHost& h = ctx->scenes[slot];
   h.used = true;
   h.alive = true;
@@ -662,25 +685,6 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
       CK_TRY(cudaMemcpyAsync(stg + 2 * bx, sc->mat, (size_t)sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload mat");
       dm_ = (const uint8_t*)(stg + 2 * bx);
     }
-  }
-  // per-particle E defaults to the material's E
-  float* dE = nullptr;
-  if (ctx->per_E) {
-    std::vector<float> Ehost;
-    // material E by index, filled on device via a temporary when materials mix is simple: upload E per particle
-    Ehost.resize((size_t)sc->n);
-    std::vector<uint8_t> mh;
-    if (sc->mat) {
-      mh.resize((size_t)sc->n);
-      if (sc->is_device)
-        CK_TRY(cudaMemcpy(mh.data(), sc->mat, (size_t)sc->n, cudaMemcpyDeviceToHost), "read mat");
-      else
-        std::memcpy(mh.data(), sc->mat, (size_t)sc->n);
-    }
-    for (int64_t i = 0; i < sc->n; ++i) Ehost[i] = (float)sc->materials[sc->mat ? mh[i] : 0].E;
-    dE = (float*)dev_alloc(ctx, sizeof(float) * (size_t)sc->n);
-    if (!dE) return fail(ctx, CKMPM_ENOMEM, "allocation failed");
-    CK_TRY(cudaMemcpyAsync(dE, Ehost.data(), sizeof(float) * sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload E");
   }
   ck::launch_admit(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur],
                    ctx->bnd[ctx->cur], ctx->d_scenes, ctx->d_mats, slot, (uint32_t)mb, (uint32_t)sc->n_materials, (uint32_t)ctx->n_cur, (uint32_t)sc->n, dx_, dv_, dm_, dE,

@@ -38,7 +38,7 @@ METRIC = "particle-steps/s at 16M particles vs quadratic B-spline; served step p
 UNIT = "particle-steps/s"
 WORKLOAD = "large_impact: 512^3 virtual grid (dx 1/512), DP sand castle + 4 FC balls (E 1e7) at 20 m/s, 16,273,664 particles, 8 ppc, dt 2e-5"
 
-# Algorithmic bytes per particle of each kernel (float32 state):
+# Algorithmic bytes per particle of each kernel (float32 state, one pass over each array):
 #   P2G: read x 12 + v 12 + M 36 B, write 2 grids x 16 B per node at 1/8 node per particle = 4 B -> 64 B
 #   G2P: read x 12 + F 36, gather 2 grids x 12 B / 8 = 3, write x 12 + v 12 + M 36 + F 36 -> 147 B
 #   grid update: per node read 16 + write 12 B, 2 grids / 8 -> 7 B

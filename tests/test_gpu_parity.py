@@ -1,6 +1,6 @@
 """Parity of the CUDA CK-MPM step (through the C ABI) with the FP64 oracle.
 
-Tolerances (stated with the benchmark spec's target and the float32 arithmetic):
+Tolerances (from the float32 arithmetic of the CUDA path):
   * grid mass and momentum after P2G: max|gpu - oracle| / max|oracle| <= 1e-5,
     per field and per grid;
   * particle positions after 100 steps of the elastic cube: <= 1e-3 dx;

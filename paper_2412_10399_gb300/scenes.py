@@ -359,3 +359,84 @@ def random_state(n: int, res: int, seed: int, margin_cells: float = 4.0,
     B = b_scale * dx * (2.0 * u[:, 6:15] - 1.0)
     F = np.eye(3)[None].repeat(n, 0).reshape(n, 9) + f_scale * (2.0 * u[:, 15:24] - 1.0)
     return x, v, B.reshape(n, 3, 3), F.reshape(n, 3, 3)
+
+
+# ----------------------------------------------------------------------------
+# declarative scenes (a JSON-friendly description of the same shapes)
+# ----------------------------------------------------------------------------
+
+_MODELS = {"fixed_corotated": FIXED_COROTATED, "drucker_prager": DRUCKER_PRAGER, "j_fluid": J_FLUID}
+_KERNELS = {"ck": KERNEL_CK, "quadratic": KERNEL_QUADRATIC}
+_TRANSFERS = {"apic_mls": TRANSFER_APIC_MLS, "pic": TRANSFER_PIC, "apic_grad": TRANSFER_APIC_GRAD}
+
+
+def _shape_of(d: dict, res: int):
+    if len(d) != 1:
+        raise ValueError(f"a shape has exactly one kind: {d!r}")
+    (kind, p), = d.items()
+    if kind == "box":
+        return _box(p["lo"], p["hi"])
+    if kind == "sphere":
+        return _sphere(p["centre"], float(p["r"]))
+    if kind == "cylinder_y":
+        return _cylinder_y(float(p["cx"]), float(p["cz"]), float(p["r"]), float(p["y0"]), float(p["y1"]))
+    raise ValueError(f"unknown shape {kind!r} (box, sphere, cylinder_y)")
+
+
+def scene_from_spec(spec: dict, seed: int = 0) -> Scene:
+    """A Scene from a plain description (the form a JSON file holds), sampled
+    by the rule of this module.  Coordinates are in cells.
+
+        {"name": "...", "res": 128, "dt": 1e-4,             # required
+         "dx": 1/res, "gravity": [0, -9.8, 0], "bc_cells": 3, "steps": 100,
+         "kernel": "ck" | "quadratic", "transfer": "apic_mls" | "pic" | "apic_grad",
+         "materials": [{"model": "fixed_corotated" | "drucker_prager" | "j_fluid",
+                        "E": ..., "nu": ..., "rho": ..., "friction_deg": 0, "gamma": 7.15}],
+         "bodies": [{"material": 0, "velocity": [vx, vy, vz],
+                     "shapes": [{"box": {"lo": [x, y, z], "hi": [x, y, z]}},
+                                {"sphere": {"centre": [x, y, z], "r": r}},
+                                {"cylinder_y": {"cx": x, "cz": z, "r": r, "y0": y, "y1": y}}]}]}
+
+    A body fills the cells whose centres lie in the union of its shapes, less
+    the cells an earlier body filled; bodies are concatenated in order."""
+    res = int(spec["res"])
+    dx = float(spec.get("dx", 1.0 / res))
+    mats = []
+    for m in spec["materials"]:
+        if m["model"] not in _MODELS:
+            raise ValueError(f"unknown material model {m['model']!r}")
+        mats.append(Material(_MODELS[m["model"]], float(m["E"]), float(m["nu"]), float(m["rho"]),
+                             float(m.get("friction_deg", 0.0)), float(m.get("gamma", 7.15))))
+    if not mats or len(mats) > 255:
+        raise ValueError("a scene has 1..255 materials")
+    xs, vs, ms = [], [], []
+    taken = np.zeros(0, np.int64)
+    for b in spec["bodies"]:
+        k = int(b.get("material", 0))
+        if not 0 <= k < len(mats):
+            raise ValueError(f"body material {k} out of range")
+        cells = filled_cells([_shape_of(s, res) for s in b["shapes"]], res)
+        cells = np.setdiff1d(cells, taken, assume_unique=True)
+        taken = np.union1d(taken, cells)
+        x = sample_cells(cells, res, dx, seed)
+        xs.append(x)
+        vs.append(np.tile(np.asarray(b.get("velocity", (0.0, 0.0, 0.0)), np.float64), (len(x), 1)))
+        ms.append(np.full(len(x), k, np.uint8))
+    if not xs or sum(len(x) for x in xs) == 0:
+        raise ValueError("the scene's bodies fill no cell")
+    kernel = spec.get("kernel", "ck")
+    transfer = spec.get("transfer", "apic_mls")
+    if kernel not in _KERNELS or transfer not in _TRANSFERS:
+        raise ValueError(f"unknown kernel {kernel!r} or transfer {transfer!r}")
+    return Scene(str(spec.get("name", "scene")), res, dx, float(spec["dt"]), np.concatenate(xs),
+                 np.concatenate(vs), np.concatenate(ms), mats,
+                 gravity=tuple(float(g) for g in spec.get("gravity", (0.0, -9.8, 0.0))),
+                 bc_cells=spec.get("bc_cells", 3), steps=int(spec.get("steps", 100)),
+                 kernel=_KERNELS[kernel], transfer=_TRANSFERS[transfer])
+
+
+def load_scene(path: str, seed: int = 0) -> Scene:
+    """scene_from_spec of a JSON file."""
+    import json
+    with open(path) as f:
+        return scene_from_spec(json.load(f), seed)

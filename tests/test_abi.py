@@ -106,3 +106,42 @@ def test_binding_structs_match_the_header_field_order():
     for name in ("ckmpm_material", "ckmpm_scene", "ckmpm_allocator", "ckmpm_config", "ckmpm_stats"):
         py = [f[0] for f in getattr(ckmpm, name)._fields_]
         assert py == structs[name], name
+
+
+def test_header_is_plain_c_and_a_c_program_links_and_calls(tmp_path):
+    """include/ckmpm.h compiles as C99 with warnings as errors, and a C program
+    linked against the library calls it (argument checks only, no GPU)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    import __graft_entry__ as g
+    g.build()
+    lib = os.path.join(ROOT, "paper_2412_10399_gb300")
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "ckmpm.h"
+int main(void) {
+  ckmpm_ctx* ctx = NULL;
+  ckmpm_scene sc;
+  memset(&sc, 0, sizeof sc);
+  if (ckmpm_create(NULL, CKMPM_KERNEL_CK | CKMPM_TRANSFER_PIC, NULL, &ctx) != CKMPM_EINVAL || ctx) return 1;
+  if (ckmpm_create(&sc, CKMPM_KERNEL_CK, NULL, &ctx) != CKMPM_EINVAL || ctx) return 2;
+  if (ckmpm_step(NULL, 1) != CKMPM_EINVAL) return 3;
+  if (ckmpm_destroy(NULL) != CKMPM_OK) return 4;
+  if (strncmp(ckmpm_version(), "ckmpm", 5) != 0) return 5;
+  printf("%s\n", ckmpm_version());
+  return 0;
+}
+''')
+    exe = tmp_path / "use"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", lib, "-lckmpm", f"-Wl,-rpath,{lib}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.startswith("ckmpm")

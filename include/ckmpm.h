@@ -12,7 +12,10 @@
  *         (Sec. 4.3.5), constitutive update (fixed-corotated, Drucker-Prager
  *         return mapping; Sec. 3.2 step 4), advection (Sec. 3.2 step 5).
  * A quadratic B-spline MLS-MPM path (single grid, 27 nodes) is built the same
- * way for comparison (Sec. 5.2 / Sec. 6.2 comparison path).
+ * way for comparison (Sec. 5.2 / Sec. 6.2 comparison path).  The transfer is
+ * selectable per context (ckmpm_transfer): APIC + MLS as above (default), PIC
+ * with the kernel gradient (Sec. 4.3), or APIC with the kernel gradient
+ * (Sec. 4.4 with the force and velocity gradient of Sec. 4.3).
  *
  * Conventions
  *  - Node i of grid k in {-1 (G-), +1 (G+)} sits at (i - k/4) dx; node indices

@@ -343,3 +343,25 @@ class Simulation:
 
     def stats(self) -> ckmpm_stats:
         return ckmpm_get_stats(self.ctx)
+
+    def save(self, path: str):
+        """Checkpoint the particle state (x, v, F and, except under the PIC
+        transfer, B; original particle order) to an .npz file."""
+        fields = {"x": self.read(FIELD_X), "v": self.read(FIELD_V), "F": self.read(FIELD_F)}
+        if not self.kernel & TRANSFER_PIC:
+            fields["B"] = self.read(FIELD_B)
+        np.savez(path, kernel=np.int64(self.kernel), **fields)
+
+    def load(self, path: str):
+        """Restore a checkpoint written by save() for the same scene and kernel
+        argument.  Order matters: positions (re-binning), velocities, F, and B
+        last, since an upload of B stores m B - dt V0 tau(F) with the F already
+        there."""
+        d = np.load(path)
+        if int(d["kernel"]) != self.kernel or d["x"].shape != (self.n, 3):
+            raise ValueError("checkpoint of another kernel argument or particle count")
+        self.write(FIELD_X, d["x"])
+        self.write(FIELD_V, d["v"])
+        self.write(FIELD_F, d["F"])
+        if "B" in d.files:
+            self.write(FIELD_B, d["B"])

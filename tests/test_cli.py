@@ -1,0 +1,73 @@
+"""The command line (python -m paper_2412_10399_gb300): scene info without a
+GPU, and the run loop's stepping and checkpoint schedule against a stand-in
+for the Simulation class."""
+import json
+
+import pytest
+
+from paper_2412_10399_gb300 import __main__ as cli
+from paper_2412_10399_gb300 import scenes as S
+
+SPEC = {"name": "two_bodies", "res": 32, "dt": 1e-4, "steps": 7,
+        "materials": [{"model": "fixed_corotated", "E": 1e5, "nu": 0.3, "rho": 1000.0},
+                      {"model": "drucker_prager", "E": 3.5e5, "nu": 0.3, "rho": 1600.0, "friction_deg": 30.0}],
+        "bodies": [{"material": 0, "shapes": [{"box": {"lo": [8, 8, 8], "hi": [12, 12, 12]}}]},
+                   {"material": 1, "velocity": [1, 0, 0], "shapes": [{"sphere": {"centre": [20, 20, 20], "r": 3}}]}]}
+
+
+@pytest.fixture
+def spec_file(tmp_path):
+    p = tmp_path / "scene.json"
+    p.write_text(json.dumps(SPEC))
+    return str(p)
+
+
+def test_info(spec_file, capsys):
+    assert cli.main(["info", spec_file]) == 0
+    info = json.loads(capsys.readouterr().out)
+    sc = S.load_scene(spec_file)
+    assert info["particles"] == sc.n == 8 * (4 ** 3 + len(S.filled_cells([S._sphere((20, 20, 20), 3.0)], 32)))
+    assert info["kernel"] == "ck" and info["transfer"] == "apic_mls"
+    assert [m["model"] for m in info["materials"]] == ["fixed_corotated", "drucker_prager"]
+    assert info["device_bytes"] > sc.n * 200
+
+
+class _FakeSim:
+    log = []
+
+    def __init__(self, sc, kernel):
+        _FakeSim.log.append(("create", sc.n, kernel))
+
+    def load(self, p):
+        _FakeSim.log.append(("load", p))
+
+    def step(self, k):
+        _FakeSim.log.append(("step", k))
+
+    def sync(self):
+        pass
+
+    def save(self, p):
+        _FakeSim.log.append(("save", p))
+        open(p, "w").close()
+
+    def close(self):
+        _FakeSim.log.append(("close",))
+
+
+def test_run_schedule(spec_file, tmp_path):
+    _FakeSim.log = []
+    sc = cli._apply_overrides(S.load_scene(spec_file), type("A", (), {"kernel": "quadratic", "transfer": "pic"}))
+    out = str(tmp_path / "frames")
+    paths = cli.run(sc, 7, 3, out, resume="r.npz", sim_cls=_FakeSim, log=lambda *a: None)
+    assert [p.rsplit("/", 1)[1] for p in paths] == ["frame_00003.npz", "frame_00006.npz", "frame_00007.npz"]
+    assert _FakeSim.log[0] == ("create", sc.n, S.KERNEL_QUADRATIC | 2)
+    assert _FakeSim.log[1] == ("load", "r.npz")
+    assert [e[1] for e in _FakeSim.log if e[0] == "step"] == [3, 3, 1]
+    assert _FakeSim.log[-1] == ("close",)
+
+
+def test_run_rejects_bad_counts(spec_file):
+    for bad in (["--steps", "0"], ["--every", "0"]):
+        with pytest.raises(SystemExit):
+            cli.main(["run", spec_file, *bad])

@@ -151,7 +151,7 @@ class EngineCK:
 
     def read(self, sid: int, field: int, n: int):
         import numpy as np
-        shape = (n, 3) if field in (0, 1) else (n, 3, 3)
+        shape = (n,) + self.ck._FIELD_SHAPE[field]
         out = np.empty(shape, np.float32)
         self.ck.ckmpm_readback(self.ctx, sid, field, out.ctypes.data, out.nbytes, False)
         return out

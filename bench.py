@@ -43,6 +43,11 @@ WORKLOAD = "large_impact: 512^3 virtual grid (dx 1/512), DP sand castle + 4 FC b
 #   G2P: read x 12 + F 36, gather 2 grids x 12 B / 8 = 3, write x 12 + v 12 + M 36 + F 36 -> 147 B
 #   grid update: per node read 16 + write 12 B, 2 grids / 8 -> 7 B
 ALGO_BYTES = {"p2g": 64.0, "g2p": 147.0, "grid_update": 7.0}
+# whole-step algorithmic bytes per particle of the compact kernel under each
+# transfer: PIC moves the same arrays; the kernel-gradient APIC adds its
+# 36-byte stress term to P2G's reads and G2P's writes
+STEP_BYTES = {"apic_mls": sum(ALGO_BYTES.values()), "pic": sum(ALGO_BYTES.values()),
+              "apic_grad": sum(ALGO_BYTES.values()) + 72.0}
 KERNEL_SLOT = {"bin": 0, "scatter": 1, "p2g": 2, "grid_update": 3, "g2p": 4, "grid_list": 5, "g2p_fp64": 6}
 
 
@@ -299,9 +304,15 @@ def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0, budget
 PAPER_DAM_BREAK_MS = {4175808: {"ck": 2.9, "quadratic": 3.7}, 8994048: {"ck": 5.7, "quadratic": 7.2}}
 
 
-def dam_break_lines(ck, stream_ptr, warmup, steps, sizes=(4175808, 8994048)):
+def _step_frac(bytes_per_particle, n, ms_per_step, peak_gbs):
+    """Whole-step algorithmic bandwidth as a fraction of the HBM peak."""
+    return bytes_per_particle * n / (ms_per_step / 1e3) / 1e9 / peak_gbs
+
+
+def dam_break_lines(ck, stream_ptr, warmup, steps, sizes=(4175808, 8994048), peak=None):
     """The paper's dam-break workload (J-based fluid, 256^3): CK and quadratic
-    ms per step over the same steps, device-resident, no per-kernel events."""
+    ms per step over the same steps, device-resident, no per-kernel events;
+    with peak (GB/s), the CK step's fraction of it."""
     from paper_2412_10399_gb300 import scenes as S
     out = {}
     for n in sizes:
@@ -316,6 +327,8 @@ def dam_break_lines(ck, stream_ptr, warmup, steps, sizes=(4175808, 8994048)):
             ck.ckmpm_destroy(ctx)
             row[name] = {"ms_per_step": ms / steps, "value": n * steps / (ms / 1e3)}
         row["ck_speedup"] = row["quadratic"]["ms_per_step"] / row["ck"]["ms_per_step"]
+        if peak:
+            row["ck"]["step_frac"] = _step_frac(STEP_BYTES["apic_mls"], n, row["ck"]["ms_per_step"], peak)
         row["paper_g2p2g_ms_rtx3090"] = PAPER_DAM_BREAK_MS.get(n)
         out[str(n)] = row
     out["workload"] = ("J-based fluid (B = 10 Pa, gamma = 7.15, rho = 1000), uniform in a cuboid at 8 per cell, "
@@ -323,11 +336,11 @@ def dam_break_lines(ck, stream_ptr, warmup, steps, sizes=(4175808, 8994048)):
     return out
 
 
-def transfer_lines(ck, scene, stream_ptr, warmup, steps):
+def transfer_lines(ck, scene, stream_ptr, warmup, steps, peak=None):
     """The kernel-gradient transfers on the headline scene and window: PIC
     (Sec. 4.3) and APIC with the kernel gradient (Sec. 4.4 with the force and
     grad v of Sec. 4.3); CK and quadratic ms per step, device-resident, no
-    per-kernel events."""
+    per-kernel events; with peak (GB/s), the CK step's fraction of it."""
     out = {}
     for tname, flag in (("pic", ck.TRANSFER_PIC), ("apic_grad", ck.TRANSFER_APIC_GRAD)):
         row = {}
@@ -340,6 +353,8 @@ def transfer_lines(ck, scene, stream_ptr, warmup, steps):
             ck.ckmpm_destroy(ctx)
             row[name] = {"ms_per_step": ms / steps, "value": scene.n * steps / (ms / 1e3)}
         row["ck_speedup"] = row["quadratic"]["ms_per_step"] / row["ck"]["ms_per_step"]
+        if peak:
+            row["ck"]["step_frac"] = _step_frac(STEP_BYTES[tname], scene.n, row["ck"]["ms_per_step"], peak)
         out[tname] = row
     out["workload"] = f"{WORKLOAD}, steps {warmup}..{warmup + steps}"
     return out
@@ -449,8 +464,9 @@ def run_gpu(args):
            "how": "admit from pinned host x/v/mat, then per step: ckmpm_step + readback of positions to pinned host"}
 
     served = served_mix(ck, stream_ptr) if not args.no_served else None
-    dam = dam_break_lines(ck, stream_ptr, args.warmup, args.steps) if not args.no_dam else None
-    transfers = transfer_lines(ck, scene, stream_ptr, args.warmup, args.steps) if not args.no_transfers else None
+    dam = dam_break_lines(ck, stream_ptr, args.warmup, args.steps, peak=peak) if not args.no_dam else None
+    transfers = (transfer_lines(ck, scene, stream_ptr, args.warmup, args.steps, peak=peak)
+                 if not args.no_transfers else None)
     cb = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:

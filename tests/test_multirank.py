@@ -45,3 +45,29 @@ def test_single_rank_aggregation():
     import bench
     value, ms = bench.aggregate_ranks(20.0, 5000, steps=10)
     assert ms == 20.0 and abs(value - 5000 * 10 / 0.02) < 1e-9
+
+
+def test_dam_break_and_transfer_lines_with_stand_in_contexts(monkeypatch):
+    """The extra bench lines, driven by stand-ins for the context calls (no
+    GPU): every row has both kernels, the speed-up and the CK step's fraction
+    of the peak from the stated algorithmic bytes."""
+    import types
+
+    import bench
+    from paper_2412_10399_gb300 import scenes as S
+    made = []
+    monkeypatch.setattr(bench, "_make_ctx", lambda ck, sc, kernel, stream: (made.append((sc.n, kernel)) or kernel, None))
+    monkeypatch.setattr(bench, "_time_steps", lambda ck, ctx, steps, stream: steps * (2.0 if ctx & 1 else 1.0))
+    fake = types.SimpleNamespace(KERNEL_CK=0, KERNEL_QUADRATIC=1, TRANSFER_PIC=2, TRANSFER_APIC_GRAD=4,
+                                 ckmpm_step=lambda c, n: None, ckmpm_sync=lambda c: None,
+                                 ckmpm_destroy=lambda c: None)
+    dam = bench.dam_break_lines(fake, 0, 1, 10, sizes=(2000,), peak=1000.0)
+    row = dam["2000"]
+    assert row["ck"]["ms_per_step"] == 1.0 and row["quadratic"]["ms_per_step"] == 2.0 and row["ck_speedup"] == 2.0
+    assert row["ck"]["step_frac"] == pytest.approx(218.0 * 2000 / 1e-3 / 1e9 / 1000.0)
+    sc = S.elastic_cube()
+    tr = bench.transfer_lines(fake, sc, 0, 1, 10, peak=1000.0)
+    assert tr["pic"]["ck"]["step_frac"] == pytest.approx(218.0 * sc.n / 1e-3 / 1e9 / 1000.0)
+    assert tr["apic_grad"]["ck"]["step_frac"] == pytest.approx(290.0 * sc.n / 1e-3 / 1e9 / 1000.0)
+    assert (sc.n, 0 | 2) in made and (sc.n, 1 | 4) in made
+    assert "step_frac" not in bench.dam_break_lines(fake, 0, 1, 10, sizes=(2000,))["2000"]["ck"]

@@ -31,6 +31,23 @@ def _apply_overrides(sc, args):
     return sc
 
 
+def cfl_number(sc) -> float:
+    """dt (c + |v|max) / dx with c the largest dilatational wave speed of the
+    scene's materials, sqrt((lam + 2 mu) / rho) for the solids and
+    sqrt(gamma B / rho) for the J-based fluid at rest volume; explicit MPM
+    wants this well below 1."""
+    import math
+    c = 0.0
+    for m in sc.materials:
+        if m.model == S.J_FLUID:
+            k = m.gamma * m.E
+        else:
+            k = m.E * (1.0 - m.nu) / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu))
+        c = max(c, math.sqrt(k / m.rho))
+    vmax = float(abs(sc.v).max()) if sc.n else 0.0
+    return sc.dt * (c + vmax) / sc.dx
+
+
 def scene_info(sc) -> dict:
     """What a scene holds and the device memory a context for it takes."""
     from .ckmpm import kernel_code
@@ -44,7 +61,7 @@ def scene_info(sc) -> dict:
             "kernel": {v: k for k, v in S._KERNELS.items()}[sc.kernel],
             "transfer": {v: k for k, v in S._TRANSFERS.items()}[sc.transfer],
             "materials": [dict(model=names[m.model], E=m.E, nu=m.nu, rho=m.rho) for m in sc.materials],
-            "device_bytes": int(mem)}
+            "device_bytes": int(mem), "cfl": cfl_number(sc)}
 
 
 def run(sc, steps: int, every: int, out: str, resume: str | None = None, sim_cls=None, log=print) -> list:
@@ -56,6 +73,9 @@ def run(sc, steps: int, every: int, out: str, resume: str | None = None, sim_cls
         from .ckmpm import Simulation as sim_cls
     from .ckmpm import kernel_code
     os.makedirs(out, exist_ok=True)
+    cfl = cfl_number(sc)
+    if cfl > 1.0:
+        log(f"warning: dt (c + |v|) / dx = {cfl:.2f} > 1; the explicit step is likely unstable")
     sim = sim_cls(sc, kernel_code(sc))
     written = []
     try:

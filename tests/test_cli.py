@@ -71,3 +71,23 @@ def test_run_rejects_bad_counts(spec_file):
     for bad in (["--steps", "0"], ["--every", "0"]):
         with pytest.raises(SystemExit):
             cli.main(["run", spec_file, *bad])
+
+
+def test_cfl_number_of_the_built_in_scenes():
+    import math
+    sc = S.elastic_cube()  # E 1e5, nu 0.3, rho 1000, at rest, dt 1e-4, dx 1/64
+    c = math.sqrt(1e5 * 0.7 / (1.3 * 0.4) / 1000.0)
+    assert cli.cfl_number(sc) == pytest.approx(1e-4 * c * 64)
+    impact = S.large_impact()  # stiff balls at 20 m/s
+    assert 0.3 < cli.cfl_number(impact) < 1.0
+    dam = S.dam_break(20000)  # fluid: sqrt(gamma B / rho)
+    assert cli.cfl_number(dam) == pytest.approx(1e-4 * math.sqrt(7.15 * 10.0 / 1000.0) * 256)
+
+
+def test_run_warns_when_dt_is_too_large(spec_file):
+    _FakeSim.log = []
+    sc = S.load_scene(spec_file)
+    sc.dt = 1.0
+    msgs = []
+    cli.run(sc, 1, 1, spec_file + "_out", sim_cls=_FakeSim, log=msgs.append)
+    assert msgs and msgs[0].startswith("warning")

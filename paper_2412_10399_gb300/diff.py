@@ -48,16 +48,29 @@ class DiffSim:
     def _p(t):
         return ctypes.c_void_p(t.data_ptr())
 
+    def _check(self, **arrays):
+        """The library reads and writes these through raw device pointers:
+        every array must be a contiguous float32 CUDA tensor of its state's
+        shape (x, v: n x 3; B, F: n x 3 x 3; E: n)."""
+        want = {"x": (self.n, 3), "v": (self.n, 3), "B": (self.n, 3, 3), "F": (self.n, 3, 3), "E": (self.n,)}
+        for name, t in arrays.items():
+            shape = want[name.lstrip("g").rstrip("1")]
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda \
+                    or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError(f"{name}: need a contiguous float32 CUDA tensor of shape {shape}")
+
     def _chk(self, st):
         if st != ck.OK:
             raise ck.CKMPMError(st, "differentiable step failed")
 
     def step(self, x, v, B, F, E) -> Tuple[torch.Tensor, ...]:
+        self._check(x=x, v=v, B=B, F=F, E=E)
         x1, v1, B1, F1 = (torch.empty_like(x), torch.empty_like(v), torch.empty_like(B), torch.empty_like(F))
         self._chk(ck.load().ckmpm_diff_step(self.h, *map(self._p, (x, v, B, F, E, x1, v1, B1, F1))))
         return x1, v1, B1, F1
 
     def step_backward(self, x, v, B, F, E, gx1, gv1, gB1, gF1, gE):
+        self._check(x=x, v=v, B=B, F=F, E=E, gx1=gx1, gv1=gv1, gB1=gB1, gF1=gF1, gE=gE)
         gx, gv, gB, gF = (torch.empty_like(x), torch.empty_like(v), torch.empty_like(B), torch.empty_like(F))
         self._chk(ck.load().ckmpm_diff_step_backward(
             self.h, *map(self._p, (x, v, B, F, E, gx1, gv1, gB1, gF1, gx, gv, gB, gF, gE))))

@@ -211,28 +211,34 @@ def ckmpm_p2g_grids_static(scene: ckmpm_scene, kernel: int, B_ptr: int, F_ptr: i
 def make_scene(res: int, dx: float, dt: float, materials, x, v=None, mat=None, gravity=(0.0, -9.8, 0.0),
                bc_cells: float = 3.0, ppc: int = 8, fp64_j_tol: float = 1e-2, fp64_cond_tol: float = 1e-2,
                fp64_gap_tol: float = 0.0):
-    """Build a ckmpm_scene from numpy arrays (host) or CUDA torch tensors.
+    """Build a ckmpm_scene from numpy arrays (host) or CUDA torch tensors:
+    x (n, 3), v (n, 3) or None, mat (n,) or None; converted to float32 /
+    uint8 and made contiguous here (the library reads them as such).
 
     Returns (scene, keepalive) where keepalive must outlive the C call."""
     keep = []
+    n = (x.shape[0] if hasattr(x, "shape") else len(x))
 
-    def ptr(a, dtype):
+    def ptr(a, dtype, name, shape):
         if a is None:
             return None, False
+        got = tuple(a.shape) if hasattr(a, "shape") else np.shape(a)
+        if got != shape:
+            raise ValueError(f"{name} has shape {got}, expected {shape}")
         if hasattr(a, "is_cuda") and a.is_cuda:
-            t = a.contiguous()
+            import torch
+            t = a.to(torch.float32 if dtype == np.float32 else torch.uint8).contiguous()
             keep.append(t)
             return t.data_ptr(), True
         arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
         keep.append(arr)
         return arr.ctypes.data, False
 
-    px, dev = ptr(x, np.float32)
-    pv, dv = ptr(v, np.float32)
-    pm, dm = ptr(mat, np.uint8)
+    px, dev = ptr(x, np.float32, "x", (n, 3))
+    pv, dv = ptr(v, np.float32, "v", (n, 3))
+    pm, dm = ptr(mat, np.uint8, "mat", (n,))
     if (pv is not None and dv != dev) or (pm is not None and dm != dev):
         raise ValueError("x, v and mat must all be host arrays or all CUDA tensors")
-    n = (x.shape[0] if hasattr(x, "shape") else len(x))
     mats = (ckmpm_material * len(materials))()
     for i, m in enumerate(materials):
         mats[i] = ckmpm_material(int(m.model), float(m.E), float(m.nu), float(m.rho), float(m.friction_deg),

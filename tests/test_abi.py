@@ -145,3 +145,26 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.startswith("ckmpm")
+
+
+def test_make_scene_checks_shapes_and_converts_types():
+    import numpy as np
+    from unittest import mock
+
+    import torch
+
+    from paper_2412_10399_gb300 import ckmpm, scenes
+    x = np.full((4, 3), 0.5)
+    for kw in ({"v": np.zeros((3, 3))}, {"v": np.zeros(12)}, {"mat": np.zeros(5, np.uint8)}):
+        with pytest.raises(ValueError):
+            ckmpm.make_scene(16, 1 / 16, 1e-4, [scenes.ELASTIC], x, **kw)
+    with pytest.raises(ValueError):
+        ckmpm.make_scene(16, 1 / 16, 1e-4, [scenes.ELASTIC], np.zeros((4, 2)))
+    sc, keep = ckmpm.make_scene(16, 1 / 16, 1e-4, [scenes.ELASTIC], x, np.zeros((4, 3)), [0, 0, 0, 0])
+    assert sc.n == 4 and keep[0].dtype == np.float32 and keep[2].dtype == np.uint8
+    # device tensors are converted on their device, not reinterpreted
+    with mock.patch.object(torch.Tensor, "is_cuda", new_callable=mock.PropertyMock, return_value=True):
+        sc, keep = ckmpm.make_scene(16, 1 / 16, 1e-4, [scenes.ELASTIC], torch.full((4, 3), 0.5, dtype=torch.float64),
+                                    torch.zeros(4, 3).t().contiguous().t(), torch.zeros(4, dtype=torch.int64))
+    assert sc.is_device == 1
+    assert keep[0].dtype == torch.float32 and keep[1].is_contiguous() and keep[2].dtype == torch.uint8

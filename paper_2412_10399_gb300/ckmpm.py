@@ -350,6 +350,14 @@ class Simulation:
     def stats(self) -> ckmpm_stats:
         return ckmpm_get_stats(self.ctx)
 
+    def diagnostics(self) -> dict:
+        """Total mass, momentum, angular momentum (with APIC's particle spin
+        where the transfer keeps B) and kinetic energy of the current state."""
+        from .diagnostics import conserved
+        B = None if self.kernel & TRANSFER_PIC else self.read(FIELD_B)
+        sc = self.scene
+        return conserved(self.read(FIELD_X), self.read(FIELD_V), sc.mat, sc.materials, sc.dx, sc.ppc, B)
+
     def save(self, path: str):
         """Checkpoint the particle state (x, v, F and, except under the PIC
         transfer, B; original particle order) to an .npz file."""

@@ -379,7 +379,13 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
   if (s->n < 1 || s->n > 0x7fffffffLL) return fail(ctx, CKMPM_EINVAL, "scene.n must be in [1, 2^31)");
   if (!s->x) return fail(ctx, CKMPM_EINVAL, "scene.x is NULL");
   if (s->res < 4 || s->res > 4096) return fail(ctx, CKMPM_EINVAL, "scene.res must be in [4, 4096]");
-  if (!(s->dx > 0) || !(s->dt > 0)) return fail(ctx, CKMPM_EINVAL, "scene.dx and scene.dt must be positive");
+  if (!(s->dx > 0) || !(s->dt > 0) || !std::isfinite(s->dx) || !std::isfinite(s->dt))
+    return fail(ctx, CKMPM_EINVAL, "scene.dx and scene.dt must be positive and finite");
+  if (!std::isfinite(s->gravity[0]) || !std::isfinite(s->gravity[1]) || !std::isfinite(s->gravity[2]))
+    return fail(ctx, CKMPM_EINVAL, "scene.gravity must be finite");
+  if (!(s->fp64_j_tol >= 0) || !(s->fp64_cond_tol >= 0) || !(s->fp64_gap_tol >= 0) || !std::isfinite(s->fp64_j_tol) ||
+      !std::isfinite(s->fp64_cond_tol) || !std::isfinite(s->fp64_gap_tol))
+    return fail(ctx, CKMPM_EINVAL, "scene.fp64_*_tol must be finite and >= 0");
   if (s->ppc < 1) return fail(ctx, CKMPM_EINVAL, "scene.ppc must be >= 1");
   if (!s->materials || s->n_materials < 1 || s->n_materials > 255)
     return fail(ctx, CKMPM_EINVAL, "scene needs 1..255 materials");
@@ -387,10 +393,12 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
     const ckmpm_material& m = s->materials[i];
     if (m.model < 0 || m.model > 2) return fail(ctx, CKMPM_EINVAL, "material.model must be 0, 1 or 2");
     if (m.model == 2 && !(m.gamma > 0)) return fail(ctx, CKMPM_EINVAL, "fluid material needs gamma > 0");
-    if (!(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0))
-      return fail(ctx, CKMPM_EINVAL, "material needs E >= 0, -1 < nu < 0.5, rho > 0");
+    if (!(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0) || !std::isfinite(m.E) || !std::isfinite(m.rho) ||
+        !std::isfinite(m.friction_deg) || (m.model == 2 && !std::isfinite(m.gamma)))
+      return fail(ctx, CKMPM_EINVAL, "material needs finite E >= 0, -1 < nu < 0.5, rho > 0");
   }
-  if (!(s->bc_cells >= 0)) return fail(ctx, CKMPM_EINVAL, "scene.bc_cells must be >= 0");
+  if (!(s->bc_cells >= 0) || !std::isfinite(s->bc_cells))
+    return fail(ctx, CKMPM_EINVAL, "scene.bc_cells must be finite and >= 0");
   return CKMPM_OK;
 }
 

@@ -98,11 +98,15 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   if (sc->n < 1 || sc->n > kStaticMaxN) return CKMPM_EINVAL;
   if (sc->res < 4 || sc->res > kStaticMaxRes) return CKMPM_EINVAL;
   if (!(sc->dx > 0) || !(sc->dt > 0) || sc->ppc < 1 || !(sc->bc_cells >= 0)) return CKMPM_EINVAL;
+  if (!std::isfinite(sc->dx) || !std::isfinite(sc->dt) || !std::isfinite(sc->bc_cells) ||
+      !std::isfinite(sc->gravity[0]) || !std::isfinite(sc->gravity[1]) || !std::isfinite(sc->gravity[2]))
+    return CKMPM_EINVAL;
   if (!sc->materials || sc->n_materials < 1 || sc->n_materials > kStaticMaxMats) return CKMPM_EINVAL;
   for (int i = 0; i < sc->n_materials; ++i) {
     const ckmpm_material& m = sc->materials[i];
     if (m.model < 0 || m.model > 2 || !(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0) ||
-        (m.model == 2 && !(m.gamma > 0)))
+        (m.model == 2 && !(m.gamma > 0)) || !std::isfinite(m.E) || !std::isfinite(m.rho) ||
+        !std::isfinite(m.friction_deg) || (m.model == 2 && !std::isfinite(m.gamma)))
       return CKMPM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;

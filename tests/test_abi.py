@@ -168,3 +168,26 @@ def test_make_scene_checks_shapes_and_converts_types():
                                     torch.zeros(4, 3).t().contiguous().t(), torch.zeros(4, dtype=torch.int64))
     assert sc.is_device == 1
     assert keep[0].dtype == torch.float32 and keep[1].is_contiguous() and keep[2].dtype == torch.uint8
+
+
+@pytest.mark.parametrize("field,value", [
+    ("dx", float("inf")), ("dt", float("nan")), ("dt", float("inf")), ("bc_cells", float("inf")),
+    ("fp64_j_tol", -1.0), ("fp64_gap_tol", float("nan")), ("gravity", (0.0, float("nan"), 0.0)),
+    ("E", float("inf")), ("rho", float("inf")), ("friction_deg", float("nan")), ("nu", 0.5), ("E", -1.0),
+])
+def test_non_finite_or_out_of_range_parameters_are_rejected(field, value):
+    """Scene and material parameters that would turn into non-finite state on
+    the device are refused with EINVAL at creation (no device work, no GPU)."""
+    import numpy as np
+    from paper_2412_10399_gb300 import ckmpm, scenes
+    mat = scenes.Material(scenes.FIXED_COROTATED, 1e5, 0.3, 1000.0, 30.0)
+    if field in ("E", "rho", "friction_deg", "nu"):
+        mat = scenes.Material(**{**mat.__dict__, field: value})
+    sc, keep = ckmpm.make_scene(16, 1 / 16, 1e-4, [mat], np.full((4, 3), 0.5, np.float32))
+    if field == "gravity":
+        sc.gravity = (ctypes.c_double * 3)(*value)
+    elif field not in ("E", "rho", "friction_deg", "nu"):
+        setattr(sc, field, value)
+    out = ctypes.c_void_p()
+    assert ckmpm.load().ckmpm_create(ctypes.byref(sc), 0, None, ctypes.byref(out)) == ckmpm.EINVAL
+    assert out.value is None

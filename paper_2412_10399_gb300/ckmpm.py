@@ -301,7 +301,11 @@ def kernel_code(scene) -> int:
 class Simulation:
     """One scene in its own context (thin wrapper over the C calls)."""
 
-    def __init__(self, scene, kernel: int = KERNEL_CK, stream: Optional[int] = None, **kw):
+    def __init__(self, scene, kernel: Optional[int] = None, stream: Optional[int] = None, **kw):
+        """kernel: the C ABI's kernel argument (ckmpm_kernel | ckmpm_transfer);
+        None takes the scene's own (kernel_code(scene))."""
+        if kernel is None:
+            kernel = kernel_code(scene)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream

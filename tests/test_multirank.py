@@ -71,3 +71,26 @@ def test_dam_break_and_transfer_lines_with_stand_in_contexts(monkeypatch):
     assert tr["apic_grad"]["ck"]["step_frac"] == pytest.approx(290.0 * sc.n / 1e-3 / 1e9 / 1000.0)
     assert (sc.n, 0 | 2) in made and (sc.n, 1 | 4) in made
     assert "step_frac" not in bench.dam_break_lines(fake, 0, 1, 10, sizes=(2000,))["2000"]["ck"]
+
+
+def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
+    """Under torchrun the oracle's reference arm runs and prints on rank 0
+    alone; the other ranks exit 0 without work."""
+    import argparse
+
+    import bench
+    called = []
+    monkeypatch.setattr(bench, "cpu_baseline", lambda steps=2: called.append(steps) or
+                        {"value": 1e5, "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "s"})
+    args = argparse.Namespace(steps=5, warmup=2, gpus=2)
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.run_reference(args) == 0
+    assert called == [] and capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    assert bench.run_reference(args) == 0
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] == 1e5
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert called == [1, 3]

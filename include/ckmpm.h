@@ -152,8 +152,8 @@ typedef struct ckmpm_ctx ckmpm_ctx;
 typedef enum {
   CKMPM_FIELD_X = 0,      /* n*3 float positions (readback, upload) */
   CKMPM_FIELD_V = 1,      /* n*3 float velocities (readback, upload) */
-  CKMPM_FIELD_B = 2,      /* n*9 float APIC matrix B, row-major (readback, upload) */
-  CKMPM_FIELD_C = 3,      /* n*9 float affine velocity gradient C = B D(x)^-1 (readback) */
+  CKMPM_FIELD_B = 2,      /* n*9 float APIC matrix B, row-major (readback, upload; zeros and no upload under PIC) */
+  CKMPM_FIELD_C = 3,      /* n*9 float affine velocity gradient C = B D(x)^-1 (readback; zeros under PIC) */
   CKMPM_FIELD_F = 4,      /* n*9 float (elastic) deformation gradient (readback, upload) */
   CKMPM_FIELD_E = 5,      /* n float per-particle Young's modulus (needs per_particle_E) */
   CKMPM_FIELD_GRID_M = 16,  /* per grid (G- then G+; one grid for quadratic) (res+1)^3 float

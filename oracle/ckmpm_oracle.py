@@ -308,16 +308,20 @@ def dp_alpha(friction_deg):
 def dp_return_map(F, mu, lam, alpha):
     """klar2016 Drucker-Prager projection of the log principal strains.
 
-    eps = ln sigma; tension (tr eps >= 0) or a purely volumetric state maps to
-    the cone tip (sigma = 1); otherwise the deviatoric part shrinks by
-    dgamma = |eps_hat| + (3 lam + 2 mu)/(2 mu) tr(eps) alpha when positive."""
+    eps = ln sigma; tension (tr eps >= 0) maps to the cone tip (sigma = 1);
+    otherwise dgamma = |eps_hat| + (3 lam + 2 mu)/(2 mu) tr(eps) alpha, and
+    the deviatoric part shrinks by dgamma when it is positive.  dgamma <= 0
+    means the state lies inside the cone and is left unchanged: a purely
+    volumetric compression (eps_hat = 0, tr eps < 0) is such a state.
+    dgamma > 0 with tr eps < 0 implies |eps_hat| > 0, so the division by
+    |eps_hat| only happens where it is defined."""
     U, s, V = svd_rv(F)
     eps = torch.log(torch.clamp(s, min=SIGMA_FLOOR))
     tr = eps.sum(-1, keepdim=True)
     eps_hat = eps - tr / 3.0
     nrm = torch.linalg.vector_norm(eps_hat, dim=-1, keepdim=True)
     dgamma = nrm + (3.0 * lam[..., None] + 2.0 * mu[..., None]) / (2.0 * mu[..., None]) * tr * alpha
-    tip = (tr >= 0.0) | (nrm <= 0.0)
+    tip = tr >= 0.0
     safe = torch.where(nrm > 0.0, nrm, torch.ones_like(nrm))
     proj = eps - dgamma * eps_hat / safe
     new_eps = torch.where(tip, torch.zeros_like(eps), torch.where(dgamma > 0.0, proj, eps))

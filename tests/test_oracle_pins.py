@@ -433,6 +433,47 @@ def test_drucker_prager_return_map_properties():
     assert torch.allclose(torch.log(s_new).sum(1), tr_e[projected], atol=1e-12)
 
 
+@pytest.mark.parametrize("c", [0.5, 0.9, 0.99, 0.995, 0.99999])
+def test_drucker_prager_keeps_isotropic_compression(c):
+    """Pure isotropic compression F = c R (c < 1, R a rotation): the log strain
+    is ln(c) (1, 1, 1), its deviator is exactly zero and tr eps < 0, so the
+    klar2016 plastic multiplier dgamma = 0 + (3 lam + 2 mu)/(2 mu) 3 ln(c) alpha
+    is negative: the state lies strictly inside the cone and the return map
+    leaves it unchanged (it is not the cone's tip, which is reserved for
+    tr eps >= 0).  The Hencky stress is then the pressure (3 lam + 2 mu) ln(c) I."""
+    mu_v, lam_v = O.lame(3.5e5, 0.3)
+    alpha = O.dp_alpha(30.0)
+    R = _rotations(4, 11)
+    F = torch.cat([c * torch.eye(3, dtype=F64)[None], c * R])
+    n = F.shape[0]
+    mu = torch.full((n,), mu_v, dtype=F64)
+    lam = torch.full((n,), lam_v, dtype=F64)
+    Fr = O.dp_return_map(F, mu, lam, alpha)
+    assert torch.allclose(Fr, F, rtol=0, atol=1e-15)
+    tau = O.hencky_kirchhoff(Fr, mu, lam)
+    p = (3.0 * lam_v + 2.0 * mu_v) * math.log(c)
+    assert torch.allclose(tau, p * torch.eye(3, dtype=F64).expand(n, 3, 3), rtol=1e-12, atol=1e-9 * mu_v)
+    # a deviatoric perturbation far below the cone's opening stays inside too
+    eps = math.log(c) * torch.ones(1, 3, dtype=F64) + torch.tensor([[1e-9, -0.5e-9, -0.5e-9]], dtype=F64)
+    Fp, _, _ = _dp_case(eps)
+    assert torch.allclose(O.dp_return_map(Fp, mu[:1], lam[:1], alpha), Fp, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("c", [1.0, 1.001, 1.1])
+def test_drucker_prager_sends_isotropic_tension_to_the_tip(c):
+    """F = c R with c >= 1 has tr eps >= 0: the cone's tip, Sigma = I, so F
+    becomes the rotation U V^T = R and carries no stress."""
+    mu_v, lam_v = O.lame(3.5e5, 0.3)
+    alpha = O.dp_alpha(30.0)
+    R = torch.cat([torch.eye(3, dtype=F64)[None], _rotations(3, 12)])
+    n = R.shape[0]
+    mu = torch.full((n,), mu_v, dtype=F64)
+    lam = torch.full((n,), lam_v, dtype=F64)
+    Fr = O.dp_return_map(c * R, mu, lam, alpha)
+    assert torch.allclose(Fr, R, rtol=0, atol=1e-14)
+    assert float(O.hencky_kirchhoff(Fr, mu, lam).abs().max()) < 1e-9 * mu_v
+
+
 def test_drucker_prager_matches_mohr_coulomb_in_triaxial_compression():
     """With alpha = sqrt(2/3) 2 sin(phi)/(3 - sin(phi)) the cone passes through
     the Mohr-Coulomb surface (cohesion 0) on the compression meridian:

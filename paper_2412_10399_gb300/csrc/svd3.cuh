@@ -244,7 +244,9 @@ __device__ __forceinline__ void hencky_tau(const T* U, const T* sig, T mu, T lam
 }
 
 // Drucker-Prager projection of the singular values (klar2016): returns true
-// when sigma changed.  Tension or a purely volumetric state goes to the tip.
+// when sigma changed.  Tension (tr eps >= 0) goes to the tip; otherwise the
+// state moves only when dgamma > 0, which with tr eps < 0 implies
+// |eps^| > 0, so a purely volumetric compression (eps^ = 0) stays inside.
 template <typename T>
 __device__ __forceinline__ bool dp_project(T* sig, T mu, T lam, T alpha) {
   T e0 = Num<T>::log_(sig[0] > T(kSigmaFloor) ? sig[0] : T(kSigmaFloor));
@@ -253,12 +255,12 @@ __device__ __forceinline__ bool dp_project(T* sig, T mu, T lam, T alpha) {
   T tr = e0 + e1 + e2;
   T h0 = e0 - tr / T(3), h1 = e1 - tr / T(3), h2 = e2 - tr / T(3);
   T nrm = Num<T>::sqrt_(h0 * h0 + h1 * h1 + h2 * h2);
-  if (tr >= T(0) || nrm <= T(0)) {
+  if (tr >= T(0)) {
     sig[0] = sig[1] = sig[2] = T(1);
     return true;
   }
   T dg = nrm + (T(3) * lam + T(2) * mu) / (T(2) * mu) * tr * alpha;
-  if (dg <= T(0)) return false;
+  if (!(dg > T(0) && nrm > T(0))) return false;  // inside the cone (nrm > 0 follows for alpha >= 0)
   T k = dg / nrm;
   sig[0] = Num<T>::exp_(e0 - k * h0);
   sig[1] = Num<T>::exp_(e1 - k * h1);
@@ -315,12 +317,12 @@ __device__ __forceinline__ void constitutive_left(int model, T* F, T mu, T lam, 
     const T nrm = Num<T>::sqrt_(h0 * h0 + h1 * h1 + h2 * h2);
     T en[3] = {ep[0], ep[1], ep[2]};
     bool moved = false;
-    if (tr >= T(0) || nrm <= T(0)) {  // tension or purely volumetric: the tip
+    if (tr >= T(0)) {  // tension: the tip
       en[0] = en[1] = en[2] = T(0);
       moved = true;
     } else {
       const T dg = nrm + (T(3) * lam + T(2) * mu) / (T(2) * mu) * tr * alpha;
-      if (dg > T(0)) {
+      if (dg > T(0) && nrm > T(0)) {
         const T k = dg / nrm;
         en[0] = ep[0] - k * h0;
         en[1] = ep[1] - k * h1;
@@ -445,7 +447,7 @@ __device__ __forceinline__ void dp_small_strain(float* F, const float* X, float 
   float Ln[6] = {L[0], L[1], L[2], L[3], L[4], L[5]};
   float Y[6];
   bool moved = false;
-  if (tr >= 0.f || nrm <= 0.f) {  // tension or purely volumetric: the tip
+  if (tr >= 0.f) {  // tension: the tip
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       Ln[q] = 0.f;
@@ -454,7 +456,7 @@ __device__ __forceinline__ void dp_small_strain(float* F, const float* X, float 
     moved = true;
   } else {
     const float dg = nrm + dpc * tr;
-    if (dg > 0.f) {
+    if (dg > 0.f && nrm > 0.f) {
       const float k = dg / nrm;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {

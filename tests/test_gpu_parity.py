@@ -277,6 +277,38 @@ def test_fp64_pass_mixed_blocks_two_steps(model):
     assert rel(vg, st2.v.numpy()) <= 2e-4
 
 
+@pytest.mark.parametrize("c,path", [(0.995, "series"), (0.9995, "series"), (1.002, "series"),
+                                    (0.9, "eigen"), (0.97, "eigen"), (1.05, "eigen"),
+                                    (0.9, "fp64"), (1.05, "fp64")])
+def test_drucker_prager_isotropic_states_each_path(c, path):
+    """Exactly isotropic F = c I through each float path of the sand update:
+    the small-stretch matrix series (|c^2 - 1| <= 1/48), the eigen-
+    decomposition of F F^T, and the float64 pass (forced by the gap
+    criterion).  Every node is a sticky wall and gravity is off, so the grid
+    velocities vanish, grad v = 0 and F reaches the return map unchanged:
+    compression (c < 1) lies inside the cone and must stay c I, tension
+    (c > 1) goes to the tip, F = I (klar2016 return map, as in the oracle)."""
+    ck = need_gpu()
+    n, res = 2000, 16
+    sc, B, _ = random_scene(n, res, 31, model=S.DRUCKER_PRAGER, gravity=(0.0, 0.0, 0.0), bc_cells=float(res))
+    F = np.broadcast_to(np.float32(c) * np.eye(3, dtype=np.float32), (n, 3, 3)).copy()
+    kw = {"fp64_gap_tol": 1.0} if path == "fp64" else {}
+    sim = ck.Simulation(sc, sc.kernel, **kw)
+    sim.write(ck.FIELD_F, F)
+    sim.step(1)
+    sim.sync()
+    n64 = int(sim.stats().fp64_particles)
+    Fg = sim.read(ck.FIELD_F)
+    vg = sim.read(ck.FIELD_V)
+    sim.close()
+    assert n64 == (n if path == "fp64" else 0)
+    assert np.all(vg == 0.0)
+    new = O.step(oracle_state(sc, np.zeros_like(B), F), O.params_from_scene(sc))
+    want = (np.float64(np.float32(c)) if c < 1.0 else 1.0) * np.eye(3)
+    assert np.abs(new.F.numpy() - want).max() <= 1e-15
+    assert np.abs(Fg - want).max() <= 2e-7 * c
+
+
 def test_upload_readback_roundtrip():
     ck = need_gpu()
     sc, B, F = random_scene(3000, 16, 11, f_scale=0.1)

@@ -95,7 +95,7 @@ typedef struct {
   double E;             /* Young's modulus [Pa]; for the fluid the equation-of-state constant B [Pa] */
   double nu;            /* Poisson ratio */
   double rho;           /* density [kg/m^3]; particle mass = rho * dx^3 / ppc */
-  double friction_deg;  /* Drucker-Prager friction angle phi [deg] */
+  double friction_deg;  /* Drucker-Prager friction angle phi [deg], in [0, 90) (else EINVAL) */
   double gamma;         /* fluid equation-of-state exponent (unused by the solids) */
 } ckmpm_material;
 
@@ -292,8 +292,15 @@ CKMPM_API ckmpm_status ckmpm_diff_destroy(ckmpm_diff* d);
  * Every call on a GPU shares that array (a previous call's leftovers are
  * cleared first), so calls that overlap on the same GPU race.  The first call
  * on each GPU looks up the array's address with that GPU current: make it
- * before any stream capture.  Returns EDOMAIN / ENONFINITE for particles
- * outside the interior or non-finite input, ECUDA on a runtime error. */
+ * before any stream capture.  With CUDA's default lazy module loading that
+ * first call is also when the 18 MiB are reserved on the GPU (with
+ * CUDA_MODULE_LOADING=EAGER, when the library's device code is loaded): a
+ * caller whose own arena will take the device memory should make one small
+ * warm-up call per GPU before the arena does, since a first call without
+ * 18 MiB free fails with ECUDA.  The call synchronises only its own stream
+ * (the error word is read back on it).  Returns EDOMAIN / ENONFINITE for
+ * particles outside the interior or non-finite input, EINVAL for a material
+ * index at or above n_materials, ECUDA on a runtime error. */
 CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* scene, int kernel, const float* B,
                                              const float* F, float* grid_m, float* grid_p, void* stream);
 

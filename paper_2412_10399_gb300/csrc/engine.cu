@@ -393,12 +393,23 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
     const ckmpm_material& m = s->materials[i];
     if (m.model < 0 || m.model > 2) return fail(ctx, CKMPM_EINVAL, "material.model must be 0, 1 or 2");
     if (m.model == 2 && !(m.gamma > 0)) return fail(ctx, CKMPM_EINVAL, "fluid material needs gamma > 0");
+    if (m.model == 1 && !(m.friction_deg >= 0 && m.friction_deg < 90))
+      return fail(ctx, CKMPM_EINVAL, "Drucker-Prager material needs a friction angle in [0, 90) degrees");
     if (!(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0) || !std::isfinite(m.E) || !std::isfinite(m.rho) ||
         !std::isfinite(m.friction_deg) || (m.model == 2 && !std::isfinite(m.gamma)))
       return fail(ctx, CKMPM_EINVAL, "material needs finite E >= 0, -1 < nu < 0.5, rho > 0");
   }
   if (!(s->bc_cells >= 0) || !std::isfinite(s->bc_cells))
     return fail(ctx, CKMPM_EINVAL, "scene.bc_cells must be finite and >= 0");
+  // host material indices are checked here, before any device work; device
+  // arrays are checked by the admission kernel (material 0 and EINVAL)
+  if (s->mat && !s->is_device) {
+    for (int64_t i = 0; i < s->n; ++i)
+      if ((int)s->mat[i] >= s->n_materials)
+        return fail(ctx, CKMPM_EINVAL,
+                    "scene.mat[" + std::to_string(i) + "] = " + std::to_string((int)s->mat[i]) +
+                        " is not below n_materials");
+  }
   return CKMPM_OK;
 }
 
@@ -608,19 +619,37 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   if (ctx->per_E) {
     std::vector<float> Ehost((size_t)sc->n);
     std::vector<uint8_t> mh;
-    if (sc->mat) {
-      mh.resize((size_t)sc->n);
-      if (sc->is_device)
-        CK_TRY(cudaMemcpy(mh.data(), sc->mat, (size_t)sc->n, cudaMemcpyDeviceToHost), "read mat");
-      else
-        std::memcpy(mh.data(), sc->mat, (size_t)sc->n);
-    }
-    for (int64_t i = 0; i < sc->n; ++i) Ehost[i] = (float)sc->materials[sc->mat ? mh[i] : 0].E;
-    dE = (float*)dev_alloc(ctx, sizeof(float) * (size_t)sc->n);
-    if (!dE) {
+    auto give_back = [&]() {
       ctx->keys_alloc.give(kb, nkeys);
       ctx->grid_alloc.give(gb, nvb);
       ctx->mat_alloc.give(mb, sc->n_materials);
+    };
+    if (sc->mat) {
+      mh.resize((size_t)sc->n);
+      cudaError_t ce = cudaSuccess;
+      if (sc->is_device)
+        ce = cudaMemcpy(mh.data(), sc->mat, (size_t)sc->n, cudaMemcpyDeviceToHost);
+      else
+        std::memcpy(mh.data(), sc->mat, (size_t)sc->n);
+      if (ce != cudaSuccess) {
+        give_back();
+        return cuda_fail(ctx, ce, "read mat");
+      }
+    }
+    // the material table is indexed on the host here, so every index is
+    // checked before it is used (the kernels check it again on the device)
+    for (int64_t i = 0; i < sc->n; ++i) {
+      const int mi = sc->mat ? (int)mh[i] : 0;
+      if (mi >= sc->n_materials) {
+        give_back();
+        return fail(ctx, CKMPM_EINVAL,
+                    "scene.mat[" + std::to_string(i) + "] = " + std::to_string(mi) + " is not below n_materials");
+      }
+      Ehost[i] = (float)sc->materials[mi].E;
+    }
+    dE = (float*)dev_alloc(ctx, sizeof(float) * (size_t)sc->n);
+    if (!dE) {
+      give_back();
       return fail(ctx, CKMPM_ENOMEM, "allocation failed");
     }
     CK_TRY(cudaMemcpyAsync(dE, Ehost.data(), sizeof(float) * sc->n, cudaMemcpyHostToDevice, ctx->stream), "upload E");

@@ -191,3 +191,21 @@ def test_non_finite_or_out_of_range_parameters_are_rejected(field, value):
     out = ctypes.c_void_p()
     assert ckmpm.load().ckmpm_create(ctypes.byref(sc), 0, None, ctypes.byref(out)) == ckmpm.EINVAL
     assert out.value is None
+
+
+def test_material_index_and_friction_angle_are_checked_before_any_device_work():
+    """A host material byte at or above n_materials, and a Drucker-Prager
+    friction angle outside [0, 90) degrees, are EINVAL before the library
+    touches the GPU (so this runs without one)."""
+    import numpy as np
+    from paper_2412_10399_gb300 import ckmpm, scenes
+    x = np.full((6, 3), 0.5, np.float32)
+    mat = np.array([0, 1, 1, 0, 2, 1], np.uint8)
+    sc, keep = ckmpm.make_scene(16, 1 / 16, 1e-4, [scenes.ELASTIC, scenes.SAND], x, mat=mat)
+    out = ctypes.c_void_p()
+    lib = ckmpm.load()
+    assert lib.ckmpm_create(ctypes.byref(sc), 0, None, ctypes.byref(out)) == ckmpm.EINVAL
+    assert out.value is None
+    bad = scenes.Material(scenes.DRUCKER_PRAGER, 3.5e5, 0.3, 1600.0, -5.0)
+    sc2, keep2 = ckmpm.make_scene(16, 1 / 16, 1e-4, [bad], x)
+    assert lib.ckmpm_create(ctypes.byref(sc2), 0, None, ctypes.byref(out)) == ckmpm.EINVAL

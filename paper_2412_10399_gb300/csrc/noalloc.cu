@@ -18,6 +18,18 @@
 // corrupt each other's results.  The first call on a GPU looks up the array's
 // device address (cudaGetSymbolAddress) with that GPU current; make that
 // first call before capturing the stream into a CUDA graph.
+//
+// When the array's memory is taken: CUDA loads a library's device code
+// lazily by default (CUDA_MODULE_LOADING=LAZY), and this file has no kernels
+// of its own, so the module that holds the array is loaded on a GPU, and its
+// 18 MiB reserved there, by the first cudaGetSymbolAddress, i.e. by the first
+// call on that GPU (with CUDA_MODULE_LOADING=EAGER, when the library's
+// context is created instead).  A caller whose own arena later claims the
+// device memory should therefore make one small warm-up call per GPU at
+// start-up, before the arena takes its share; a first call made after the
+// memory is gone fails with CKMPM_ECUDA.  The call waits for its own work on
+// its stream only: the error word is read back with an asynchronous copy on
+// that stream followed by a synchronisation of that stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,6 +116,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   if (!sc->materials || sc->n_materials < 1 || sc->n_materials > kStaticMaxMats) return CKMPM_EINVAL;
   for (int i = 0; i < sc->n_materials; ++i) {
     const ckmpm_material& m = sc->materials[i];
+    if (m.model == 1 && !(m.friction_deg >= 0 && m.friction_deg < 90)) return CKMPM_EINVAL;
     if (m.model < 0 || m.model > 2 || !(m.E >= 0) || !(m.nu > -1.0 && m.nu < 0.5) || !(m.rho > 0) ||
         (m.model == 2 && !(m.gamma > 0)) || !std::isfinite(m.E) || !std::isfinite(m.rho) ||
         !std::isfinite(m.friction_deg) || (m.model == 2 && !std::isfinite(m.gamma)))
@@ -257,9 +270,11 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   ck::launch_read_grid(kernel, st, v, 0, 0, grid_m);
   ck::launch_read_grid(kernel, st, v, 0, 1, grid_p);
   CK_S(cudaGetLastError());
-  CK_S(cudaStreamSynchronize(st));
+  // the error word comes back on the caller's stream: waiting for that
+  // stream alone leaves work on the device's other streams running
   uint32_t err = 0;
-  CK_S(cudaMemcpy(&err, v.err, sizeof(err), cudaMemcpyDeviceToHost));
+  CK_S(cudaMemcpyAsync(&err, v.err, sizeof(err), cudaMemcpyDeviceToHost, st));
+  CK_S(cudaStreamSynchronize(st));
 #undef CK_S
   if (err & CK_ERR_NONFINITE) return CKMPM_ENONFINITE;
   if (err & CK_ERR_DOMAIN) return CKMPM_EDOMAIN;

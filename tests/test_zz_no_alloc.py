@@ -21,10 +21,11 @@ from paper_2412_10399_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 
-def _context_grids(ck, sc, B, F):
-    sim = ck.Simulation(sc, sc.kernel)
+def _context_grids(ck, sc, B, F, transfer=0):
+    sim = ck.Simulation(sc, sc.kernel | transfer)
     sim.write(ck.FIELD_F, F)
-    sim.write(ck.FIELD_B, B)
+    if B is not None:
+        sim.write(ck.FIELD_B, B)
     sim.probe_grids()
     gm = sim.read(ck.FIELD_GRID_M)
     gp = sim.read(ck.FIELD_GRID_P)
@@ -32,22 +33,40 @@ def _context_grids(ck, sc, B, F):
     return gm, gp
 
 
-def _static_grids(ck, sc, B, F):
-    dev = torch.device("cuda")
-    x = torch.from_numpy(f32(sc.x)).to(dev)
-    v = torch.from_numpy(f32(sc.v)).to(dev)
-    mat = torch.from_numpy(sc.mat.copy()).to(dev)
-    Bd = torch.from_numpy(B.reshape(-1, 9).copy()).to(dev)
-    Fd = torch.from_numpy(F.reshape(-1, 9).copy()).to(dev)
-    ng = 2 if sc.kernel == S.KERNEL_CK else 1
-    nn = sc.res + 1
-    gm = torch.empty((ng, nn, nn, nn), dtype=torch.float32, device=dev)
-    gp = torch.empty((ng, nn, nn, nn, 3), dtype=torch.float32, device=dev)
-    scs, keep = ck.make_scene(sc.res, sc.dx, sc.dt, sc.materials, x, v, mat, gravity=sc.gravity,
-                              bc_cells=sc.bc_cells, ppc=sc.ppc)
-    stream = torch.cuda.current_stream().cuda_stream
-    ck.ckmpm_p2g_grids_static(scs, sc.kernel, Bd.data_ptr(), Fd.data_ptr(), gm.data_ptr(), gp.data_ptr(), stream)
-    return gm.cpu().numpy(), gp.cpu().numpy()
+class _StaticCall:
+    """Device inputs and outputs of one scene, allocated up front, so that a
+    call of the entry point itself needs no memory from anyone."""
+
+    def __init__(self, ck, sc, B, F, transfer=0):
+        dev = torch.device("cuda")
+        self.ck, self.kernel = ck, sc.kernel | transfer
+        self.x = torch.from_numpy(f32(sc.x)).to(dev)
+        self.v = torch.from_numpy(f32(sc.v)).to(dev)
+        self.mat = torch.from_numpy(sc.mat.copy()).to(dev)
+        self.B = None if B is None else torch.from_numpy(B.reshape(-1, 9).copy()).to(dev)
+        self.F = torch.from_numpy(F.reshape(-1, 9).copy()).to(dev)
+        ng = 2 if sc.kernel == S.KERNEL_CK else 1
+        nn = sc.res + 1
+        self.gm = torch.empty((ng, nn, nn, nn), dtype=torch.float32, device=dev)
+        self.gp = torch.empty((ng, nn, nn, nn, 3), dtype=torch.float32, device=dev)
+        self.scs, self.keep = ck.make_scene(sc.res, sc.dx, sc.dt, sc.materials, self.x, self.v, self.mat,
+                                            gravity=sc.gravity, bc_cells=sc.bc_cells, ppc=sc.ppc)
+        self.stream = torch.cuda.current_stream().cuda_stream
+
+    def __call__(self):
+        self.ck.ckmpm_p2g_grids_static(self.scs, self.kernel, 0 if self.B is None else self.B.data_ptr(),
+                                       self.F.data_ptr(), self.gm.data_ptr(), self.gp.data_ptr(), self.stream)
+        return self.gm.cpu().numpy(), self.gp.cpu().numpy()
+
+
+def _static_grids(ck, sc, B, F, transfer=0):
+    return _StaticCall(ck, sc, B, F, transfer)()
+
+
+def _check(gm, gp, gm_ref, gp_ref):
+    for g in range(gm.shape[0]):
+        assert rel(gm[g], gm_ref[g]) <= 1e-5
+        assert np.abs(gp[g] - gp_ref[g]).max() <= 1e-5 * np.abs(gp_ref[g]).max()
 
 
 @pytest.mark.parametrize("kernel", [S.KERNEL_CK, S.KERNEL_QUADRATIC])
@@ -58,9 +77,38 @@ def test_static_p2g_matches_context_path_on_two_calls(kernel):
                                 kernel=kernel, f_scale=0.08)
         gm_ref, gp_ref = _context_grids(ck, sc, B, F)
         gm, gp = _static_grids(ck, sc, B, F)
-        for g in range(gm.shape[0]):
-            assert rel(gm[g], gm_ref[g]) <= 1e-5
-            assert np.abs(gp[g] - gp_ref[g]).max() <= 1e-5 * np.abs(gp_ref[g]).max()
+        _check(gm, gp, gm_ref, gp_ref)
+
+
+def test_static_p2g_pic_matches_a_pic_context_on_two_calls():
+    """The PIC transfer (no B; force from the kernel gradient) on the same
+    fixed array, against a context created with CKMPM_TRANSFER_PIC."""
+    ck = need_gpu()
+    for n, res, seed in ((9000, 32, 24), (3000, 24, 25)):
+        sc, _, F = random_scene(n, res, seed, model=S.FIXED_COROTATED, f_scale=0.08)
+        gm_ref, gp_ref = _context_grids(ck, sc, None, F, transfer=ck.TRANSFER_PIC)
+        gm, gp = _static_grids(ck, sc, None, F, transfer=ck.TRANSFER_PIC)
+        _check(gm, gp, gm_ref, gp_ref)
+
+
+def test_static_p2g_at_its_limits_takes_no_device_memory():
+    """At the stated limits (65,536 particles on a 64^3 grid) the fixed array
+    is large enough, and a call takes no device memory: with the inputs and
+    outputs allocated beforehand and one warm-up call made (the first call on
+    a GPU reserves the array and loads the kernels), the device's free memory
+    is the same before and after a second call."""
+    ck = need_gpu()
+    sc, B, F = random_scene(65536, 64, 26, model=S.DRUCKER_PRAGER, f_scale=0.08)
+    gm_ref, gp_ref = _context_grids(ck, sc, B, F)
+    call = _StaticCall(ck, sc, B, F)
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    gm, gp = call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    _check(gm, gp, gm_ref, gp_ref)
 
 
 def test_static_p2g_rejects_sizes_beyond_its_limits():

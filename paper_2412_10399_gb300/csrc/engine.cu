@@ -440,6 +440,10 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   ctx->lc.g2p_minb = ctx->kind == 0 ? 5 : 4;
   ctx->lc.transfer = ctx->transfer == CKMPM_TRANSFER_PIC ? 1 : ctx->transfer == CKMPM_TRANSFER_APIC_GRAD ? 2 : 0;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
+  // two copies of the P2G accumulators are the faster choice for the
+  // quadratic twin (27-node stencils collide more), one for the compact kernel
+  ctx->lc.p2g_rep = ctx->kind == 1 ? 2 : 1;
+  if (const char* e = getenv("CKMPM_P2G_REP")) ctx->lc.p2g_rep = atoi(e) == 2 ? 2 : 1;
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {

@@ -14,6 +14,7 @@ struct LaunchCfg {
   int sm_count = 1;     // SMs of the device (grid of the float64 pass)
   int g2p_minb = 4;     // resident G2P warps per SM / 4 the register budget targets
   int transfer = 0;     // 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient
+  int p2g_rep = 1;      // copies of the P2G shared accumulators (1 or 2)
 };
 
 enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4 };

@@ -675,13 +675,28 @@ __device__ __forceinline__ void p2g_scatter_grad(const SceneDev& s, const MatDev
   });
 }
 
+// Replicated accumulators: with REP = 2 the staged sums exist twice and a
+// lane adds into copy (lane & 1).  Lanes of one cell are neighbours (they
+// take particles C apart in binned order), and k lanes on one shared address
+// cost about k cycles, so splitting neighbours over two copies halves those
+// collisions; the copies start 16 banks apart, so the same node in both
+// copies is on different banks.  The copies are summed at the flush.
+template <int KIND, int REP>
+struct P2GRep {
+  static constexpr int NS = Geo<KIND>::NS;
+  static constexpr int stride = REP == 1 ? 4 * NS : ((4 * NS + 15) / 32) * 32 + 16;  // ints per copy
+};
+
 // TR: transfer, 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient.
-template <int KIND, int TR>
+template <int KIND, int TR, int REP>
 __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
+  constexpr int RS = P2GRep<KIND, REP>::stride;
   constexpr uint32_t CAP = kP2GStage, C = kP2GStage / 32;
   static_assert(C % 2 == 1, "lane stride must be odd");
-  __shared__ __align__(16) int sm[4][NS];
+  static_assert(RS % 4 == 0, "copies must keep 16-byte alignment");
+  __shared__ __align__(16) int small[REP * RS];
+  int(*sm)[NS] = reinterpret_cast<int(*)[NS]>(small + (REP == 1 ? 0 : (int)(threadIdx.x & 1u) * RS));
   __shared__ float4 sX[CAP], sA[CAP], sB[CAP], sC[CAP];
   constexpr uint32_t TCAP = TR == 2 ? CAP : 1;  // the stress term T (kernel-gradient APIC only)
   __shared__ float4 sT0[TCAP], sT1[TCAP];
@@ -706,7 +721,7 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
-    for (int j = lane; j < NS; j += kP2GWarp) reinterpret_cast<int4*>(&sm[0][0])[j] = make_int4(0, 0, 0, 0);
+    for (int j = lane; j < REP * RS / 4; j += kP2GWarp) reinterpret_cast<int4*>(small)[j] = make_int4(0, 0, 0, 0);
     const float fcnt = (float)cnt;
     const float Sm = bmass > 0.f ? 1073741824.0f / (fcnt * bmass) : 1.0f;
     const float Sp = bmom > 0.f ? 1073741824.0f / (fcnt * bmom) : 1.0f;
@@ -750,14 +765,21 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
     }
     const float iSm = 1.0f / Sm, iSp = 1.0f / Sp;
     for (int j = lane; j < NS; j += kP2GWarp) {
-      int mi = sm[0][j];
-      if (mi != 0) {
+      // the copies' sums: each copy's sum is bounded like the whole, and
+      // their total too, so adding them as integers cannot overflow
+      int q[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        q[c] = small[c * NS + j];
+        if (REP == 2) q[c] += small[RS + c * NS + j];
+      }
+      if (q[0] != 0) {
         int g, lx, ly, lz;
         staged_coords<KIND>(j, g, lx, ly, lz);
         long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
         if (gi >= 0)
-          atomicAdd(&v.Gacc[gi], make_float4((float)mi * iSm, (float)sm[1][j] * iSp, (float)sm[2][j] * iSp,
-                                             (float)sm[3][j] * iSp));
+          atomicAdd(&v.Gacc[gi], make_float4((float)q[0] * iSm, (float)q[1] * iSp, (float)q[2] * iSp,
+                                             (float)q[3] * iSp));
       }
     }
     // the bounds are used: clear them for the step that next bins into this
@@ -1405,11 +1427,13 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
     case LK_P2G:
       if (lc.transfer == 1)
-        k_p2g<KIND, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+        k_p2g<KIND, 1, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       else if (lc.transfer == 2)
-        k_p2g<KIND, 2><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+        k_p2g<KIND, 2, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+      else if (lc.p2g_rep == 2)
+        k_p2g<KIND, 0, 2><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       else
-        k_p2g<KIND, 0><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+        k_p2g<KIND, 0, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       break;
     // a wide grid: each CTA's block loop is short, so the dependent loads of
     // one block (list entry, scene, accumulators) overlap across CTAs

@@ -80,6 +80,18 @@ typedef enum {
   CKMPM_TRANSFER_PIC = 2,
   CKMPM_TRANSFER_APIC_GRAD = 4
 } ckmpm_transfer;
+/* Step structure, OR-ed into a kernel argument (ckmpm_create, ckmpm_config):
+ *   CKMPM_STEP_G2P2G: the fused step of Sec. 5.1 (G2P of step n and P2G of
+ *     step n + 1 in one kernel, after Wang 2020) in place of separate P2G and
+ *     G2P kernels; APIC + MLS transfer only (else EINVAL).  Each CTA gathers
+ *     a particle block of step n and scatters the particles that stay in
+ *     that block into the next step's grid; particles that move to another
+ *     block (or take the float64 pass) are scattered by a second, small
+ *     kernel.  Results match the split step within float32 rounding.  The
+ *     context keeps a second block table (one entry per virtual grid block)
+ *     and a particle list.  After an admission, release, upload or probe the
+ *     next step first recomputes the current grid with the split kernels. */
+typedef enum { CKMPM_STEP_SPLIT = 0, CKMPM_STEP_G2P2G = 8 } ckmpm_step_mode;
 typedef enum { CKMPM_FIXED_COROTATED = 0, CKMPM_DRUCKER_PRAGER = 1, CKMPM_J_FLUID = 2 } ckmpm_model;
 
 /* Constitutive parameters of one material.  Lame parameters are
@@ -134,7 +146,7 @@ typedef struct {
 /* Capacities of a multi-scene context (a "server"): all resident scenes step
  * together in one launch per kernel over their concatenated block lists. */
 typedef struct {
-  int kernel;                  /* ckmpm_kernel | ckmpm_transfer; fixed for the context */
+  int kernel;                  /* ckmpm_kernel | ckmpm_transfer | ckmpm_step_mode; fixed for the context */
   int64_t max_particles;       /* particle pool capacity */
   int64_t max_keys;            /* particle-block key space (sum over scenes of ceil(res/4)^3) */
   int64_t max_grid_blocks;     /* grid pool: 4x4x4-node blocks active at once, all scenes together */
@@ -171,14 +183,17 @@ typedef struct {
   double ms_last_step;        /* device time of the last step (timing on) */
   double ms_kernel[8];        /* average device ms per launch per kernel since the
                                  last ckmpm_reset_timing(): 0 bin, 1 scatter,
-                                 2 p2g, 3 grid update, 4 g2p, 5 grid list,
-                                 6 float64 pass */
+                                 2 p2g (fused steps: the leftover P2G), 3 grid
+                                 update, 4 g2p, 5 grid list, 6 float64 pass,
+                                 7 fused G2P2G */
   int64_t launches_kernel[8]; /* launches counted in ms_kernel */
   int64_t launches_per_step;  /* kernel launches issued by one step */
+  int64_t leftover_particles; /* fused steps: particles of the last step's leftover P2G */
 } ckmpm_stats;
 
 /* Create a context holding one scene (scene id 0) with capacities equal to
- * that scene.  kernel: ckmpm_kernel | ckmpm_transfer.  stream: cudaStream_t or NULL.
+ * that scene.  kernel: ckmpm_kernel | ckmpm_transfer | ckmpm_step_mode.
+ * stream: cudaStream_t or NULL.
  * Errors: EINVAL (bad scene), ENOMEM, ECUDA.  *out is NULL on error. */
 CKMPM_API ckmpm_status ckmpm_create(const ckmpm_scene* scene, int kernel, void* stream, ckmpm_ctx** out);
 

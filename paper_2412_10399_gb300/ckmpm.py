@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libckmpm.so")
 OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ENONFINITE, ETIMEOUT, EBUSY, ENOTFOUND = range(9)
 KERNEL_CK, KERNEL_QUADRATIC = 0, 1
 TRANSFER_APIC_MLS, TRANSFER_PIC, TRANSFER_APIC_GRAD = 0, 2, 4  # OR-ed into a kernel argument
+STEP_SPLIT, STEP_G2P2G = 0, 8  # step structure, OR-ed into a kernel argument
 FIXED_COROTATED, DRUCKER_PRAGER, J_FLUID = 0, 1, 2
 FIELD_X, FIELD_V, FIELD_B, FIELD_C, FIELD_F, FIELD_E = 0, 1, 2, 3, 4, 5
 FIELD_GRID_M, FIELD_GRID_P, FIELD_GRID_V = 16, 17, 18
@@ -62,7 +63,7 @@ class ckmpm_stats(ctypes.Structure):
                 ("n_grid_blocks", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("fp64_particles", ctypes.c_int64), ("ms_last_step", ctypes.c_double),
                 ("ms_kernel", ctypes.c_double * 8), ("launches_kernel", ctypes.c_int64 * 8),
-                ("launches_per_step", ctypes.c_int64)]
+                ("launches_per_step", ctypes.c_int64), ("leftover_particles", ctypes.c_int64)]
 
 
 # Every symbol the header declares, with its signature.

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(StepView v, BinScratch bs, ui
     *v.fp64_count = 0ull;
     v.work[0] = 0u;
     v.work[1] = 0u;
+    if (v.lo_count) *v.lo_count = 0u;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -253,6 +254,21 @@ __global__ void k_glist(StepView v, uint32_t n_vblocks) {
       v.gflag[g] = 0u;
     }
   }
+}
+
+// Fused step: before a block table is filled again, the entries its last
+// use assigned (the first *n_g entries of its list, slots claimed by the
+// leftover P2G included) go back to CK_NO_SLOT, so that every entry not
+// assigned in this step reads as unassigned.
+__global__ void k_table_reset(uint32_t* table, const uint32_t* g_list, const uint32_t* n_g, uint32_t pool_cap) {
+  const uint32_t n = min(*n_g, pool_cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    table[g_list[i]] = CK_NO_SLOT;
+}
+
+void launch_table_reset(cudaStream_t st, uint32_t* table, const uint32_t* g_list, const uint32_t* n_g,
+                        uint32_t pool_cap, int grid_ctas) {
+  k_table_reset<<<grid_ctas, 256, 0, st>>>(table, g_list, n_g, pool_cap);
 }
 
 // Retire particles [start, start + n) of the current pool (a released scene):

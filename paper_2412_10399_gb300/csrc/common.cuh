@@ -112,6 +112,16 @@ struct StepView {
   uint32_t n_keys;      // size of the key space
   uint32_t n_cur;       // particles in cur (including dead ones)
   uint32_t keep_gacc;   // probe: the grid update leaves Gacc, P2G keeps bnd_cur
+  // fused G2P2G step only (else null): the block table of the next step's
+  // grid (the gather reads Gvel through `table`, the scatter adds to Gacc
+  // through these), and the list of particles the fused kernel leaves to the
+  // leftover P2G (changed block, float64 pass, non-finite)
+  uint32_t* table_nxt;
+  uint32_t* g_list_nxt;
+  uint32_t* g_scene_nxt;
+  uint32_t* n_g_nxt;
+  uint32_t* lo_list;
+  uint32_t* lo_count;
 };
 
 __device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }

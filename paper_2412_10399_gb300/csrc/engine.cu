@@ -102,7 +102,14 @@ struct ckmpm_ctx {
   uint32_t* cnt[2]{};
   uint32_t* bnd[2]{};  // per key: P2G contribution bounds (2 floats as bits)
   uint32_t *offset = nullptr, *cursor = nullptr, *perm = nullptr, *pb_key = nullptr, *pb_scene = nullptr;
-  uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit), [6..7] work
+  uint32_t *counters = nullptr;  // [0] n_pb, [1] n_g, [2] err, [4..5] fp64 (64-bit), [6..7] work,
+                                 // [8] n_g of the second table set, [9] leftover count
+  // fused G2P2G steps: a second block-table set for the next step's grid,
+  // which one maps the current grid velocities, and whether they are current
+  bool fused = false;
+  int tsel = 0;
+  bool grid_valid = false;
+  uint32_t *table1 = nullptr, *g_list1 = nullptr, *g_scene1 = nullptr, *lo_list = nullptr;
   uint32_t* fp64_list = nullptr;  // particles of the float64 pass (capacity cap_n)
   uint32_t *gflag = nullptr, *table = nullptr, *g_list = nullptr, *g_scene = nullptr;
   uint32_t *tile_cnt = nullptr, *tile_ne = nullptr, *scene_tab = nullptr;
@@ -219,16 +226,16 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.pb_key = ctx->pb_key;
   v.pb_scene = ctx->pb_scene;
   v.n_pb = ctx->counters + 0;
-  v.n_g = ctx->counters + 1;
+  v.n_g = ctx->counters + (ctx->tsel == 0 ? 1 : 8);
   v.err = ctx->counters + 2;
   v.fp64_count = (unsigned long long*)(ctx->counters + 4);
   v.fp64_list = ctx->fp64_list;
   v.work = ctx->counters + 6;
   v.gflag = ctx->gflag;
-  v.table = ctx->table;
+  v.table = ctx->tsel == 0 ? ctx->table : ctx->table1;
   v.pool_cap = (uint32_t)ctx->cap_pool;
-  v.g_list = ctx->g_list;
-  v.g_scene = ctx->g_scene;
+  v.g_list = ctx->tsel == 0 ? ctx->g_list : ctx->g_list1;
+  v.g_scene = ctx->tsel == 0 ? ctx->g_scene : ctx->g_scene1;
   v.Gacc = ctx->Gacc;
   v.Gvel = ctx->Gvel;
   v.scenes = ctx->d_scenes;
@@ -236,6 +243,10 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.n_keys = (uint32_t)std::max<int64_t>(ctx->keys_alloc.high, 1);
   v.n_cur = (uint32_t)ctx->n_cur;
   v.keep_gacc = 0;
+  if (ctx->fused) {  // binning zeroes the leftover count every step
+    v.lo_list = ctx->lo_list;
+    v.lo_count = ctx->counters + 9;
+  }
   return v;
 }
 
@@ -414,11 +425,15 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
 }
 
 ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
-  if (cfg->kernel < 0 || cfg->kernel > 5)
+  if ((cfg->kernel & ~15) != 0 || (cfg->kernel & 6) == 6)
     return fail(ctx, CKMPM_EINVAL,
-                "kernel must be 0 (CK) or 1 (quadratic), optionally | CKMPM_TRANSFER_PIC or CKMPM_TRANSFER_APIC_GRAD");
+                "kernel must be 0 (CK) or 1 (quadratic), optionally | CKMPM_TRANSFER_PIC or CKMPM_TRANSFER_APIC_GRAD, "
+                "and | CKMPM_STEP_G2P2G");
   ctx->kind = cfg->kernel & 1;
   ctx->transfer = cfg->kernel & 6;
+  ctx->fused = (cfg->kernel & CKMPM_STEP_G2P2G) != 0;
+  if (ctx->fused && ctx->transfer != CKMPM_TRANSFER_APIC_MLS)
+    return fail(ctx, CKMPM_EINVAL, "the fused G2P2G step takes the APIC + MLS transfer only");
   if (cfg->max_particles < 1 || cfg->max_keys < 1 || cfg->max_grid_blocks < 1 || cfg->max_virtual_blocks < 1 ||
       cfg->max_scenes < 1 ||
       cfg->max_scenes > 1024 || cfg->max_materials < 1 || cfg->max_materials > 65535)
@@ -466,7 +481,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
             alloc_n(ctx, ctx->cnt[1], ctx->cap_keys) && alloc_n(ctx, ctx->bnd[0], 2 * ctx->cap_keys) &&
             alloc_n(ctx, ctx->bnd[1], 2 * ctx->cap_keys) && alloc_n(ctx, ctx->offset, ctx->cap_keys) &&
             alloc_n(ctx, ctx->cursor, ctx->cap_keys) && alloc_n(ctx, ctx->pb_key, ctx->cap_keys) &&
-            alloc_n(ctx, ctx->pb_scene, ctx->cap_keys) && alloc_n(ctx, ctx->counters, 8) &&
+            alloc_n(ctx, ctx->pb_scene, ctx->cap_keys) && alloc_n(ctx, ctx->counters, 12) &&
             alloc_n(ctx, ctx->gflag, ctx->cap_vblocks) && alloc_n(ctx, ctx->table, ctx->cap_vblocks) &&
             alloc_n(ctx, ctx->g_list, ctx->cap_pool) && alloc_n(ctx, ctx->g_scene, ctx->cap_pool) &&
             alloc_n(ctx, ctx->tile_cnt, ceil_div(ctx->cap_keys, ck::kScanTile) + 1) &&
@@ -475,12 +490,16 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
             alloc_n(ctx, ctx->Gacc, ctx->cap_pool * NG * ck::kBlockNodes) &&
             alloc_n(ctx, ctx->Gvel, ctx->cap_pool * NG * ck::kBlockNodes) &&
             alloc_n(ctx, ctx->d_scenes, ctx->cap_scenes) && alloc_n(ctx, ctx->d_mats, ctx->cap_mats);
+  if (ok && ctx->fused)
+    ok = alloc_n(ctx, ctx->table1, ctx->cap_vblocks) && alloc_n(ctx, ctx->g_list1, ctx->cap_pool) &&
+         alloc_n(ctx, ctx->g_scene1, ctx->cap_pool) && alloc_n(ctx, ctx->lo_list, ctx->cap_n);
   if (!ok) return fail(ctx, CKMPM_ENOMEM, "device memory allocation failed");
+  if (ctx->fused) CK_TRY(cudaMemsetAsync(ctx->table1, 0xff, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->cnt[0], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->cnt[1], 0, sizeof(uint32_t) * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->bnd[0], 0, sizeof(uint32_t) * 2 * ctx->cap_keys, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->bnd[1], 0, sizeof(uint32_t) * 2 * ctx->cap_keys, ctx->stream), "memset");
-  CK_TRY(cudaMemsetAsync(ctx->counters, 0, sizeof(uint32_t) * 8, ctx->stream), "memset");
+  CK_TRY(cudaMemsetAsync(ctx->counters, 0, sizeof(uint32_t) * 12, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->gflag, 0, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->table, 0xff, sizeof(uint32_t) * ctx->cap_vblocks, ctx->stream), "memset");
   CK_TRY(cudaMemsetAsync(ctx->Gacc, 0, sizeof(float4) * ctx->cap_pool * NG * ck::kBlockNodes, ctx->stream), "memset");
@@ -508,9 +527,11 @@ bool capturing(ckmpm_ctx* ctx) {
   return st != cudaStreamCaptureStatusNone;
 }
 
+ckmpm_status run_step_fused(ckmpm_ctx* ctx);
+
 ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
-  const int NG = ctx->kind == 0 ? 2 : 1;
-  (void)NG;
+  if (ctx->fused && !probe) return run_step_fused(ctx);
+  if (ctx->fused) ctx->grid_valid = false;  // a probe reuses the grid arrays
   ck::StepView v = make_view(ctx);
   ckmpm_ctx::EvPair ep{};
   if (ctx->grids_dirty) {
@@ -541,6 +562,9 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   ck::BinScratch bs = make_bs(ctx, n_scene_tab(ctx));
   const uint32_t ngb = (uint32_t)std::max<int64_t>(ctx->grid_alloc.high, 1);
   const int grid_ctas = ctx->sm_count * 4;
+  // fused contexts keep each table set's assigned entries listed, so that a
+  // set is cleared before it is filled again (a probe fills set tsel)
+  if (ctx->fused) ck::launch_table_reset(ctx->stream, v.table, v.g_list, v.n_g, v.pool_cap, grid_ctas);
   if (ctx->timing && !probe) cudaEventRecord(ctx->step_a, ctx->stream);
   tbeg(ctx, ep, 0);
   ck::launch_bin(ctx->stream, v, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
@@ -574,6 +598,114 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   if (ctx->timing) cudaEventRecord(ctx->step_b, ctx->stream);
   CK_TRY(cudaGetLastError(), "step launch");
   ctx->cur ^= 1;
+  ctx->n_cur = n_live;
+  rebuild_layout_sorted(ctx);
+  ctx->steps++;
+  process_pending(ctx);
+  return CKMPM_OK;
+}
+
+// One fused step (CKMPM_STEP_G2P2G).  The grid of the current state (Gvel
+// through block-table set tsel) comes from the previous fused step, or from
+// a prologue that runs the split path's binning, P2G and grid update when
+// the state changed outside a step (admission, release, upload, probe).
+// Then: the other table set is cleared of its last use and filled from this
+// step's particle blocks (2x2x2 grid blocks each); the fused kernel runs G2P
+// and scatters the particles that stayed in their block into that grid; the
+// float64 pass; the leftover P2G (claiming any further grid blocks); the grid
+// update of the new grid; and the sets swap.
+ckmpm_status run_step_fused(ckmpm_ctx* ctx) {
+  if (ctx->grids_dirty) {
+    ck::launch_transfer(ctx->kind, ctx->lc, make_view(ctx), ck::LK_CLEAR);
+    ctx->grids_dirty = false;
+    ctx->grid_valid = false;
+  }
+  if (ctx->keys_dirty) {
+    ck::StepView v = make_view(ctx);
+    CK_TRY(cudaMemsetAsync(ctx->cnt[ctx->cur], 0, sizeof(uint32_t) * v.n_keys, ctx->stream), "memset");
+    CK_TRY(cudaMemsetAsync(ctx->bnd[ctx->cur], 0, sizeof(uint32_t) * 2 * v.n_keys, ctx->stream), "memset");
+    if (ctx->n_cur > 0)
+      ck::launch_rekey(ctx->kind, ctx->stream, ctx->pool[ctx->cur], ctx->key[ctx->cur], ctx->cnt[ctx->cur],
+                       ctx->bnd[ctx->cur], ctx->d_scenes, ctx->d_mats, (uint32_t)ctx->n_cur, v.err);
+    ctx->keys_dirty = false;
+    ctx->grid_valid = false;
+  }
+  int64_t n_live = 0;
+  for (auto& s : ctx->scenes) n_live += s.alive ? s.n : 0;
+  if (n_live == 0) {
+    ctx->n_cur = 0;
+    ctx->layout.clear();
+    ctx->steps++;
+    process_pending(ctx);
+    ctx->grid_valid = false;
+    CK_TRY(cudaGetLastError(), "step launch");
+    return CKMPM_OK;
+  }
+  ck::BinScratch bs = make_bs(ctx, n_scene_tab(ctx));
+  const uint32_t ngb = (uint32_t)std::max<int64_t>(ctx->grid_alloc.high, 1);
+  const int grid_ctas = ctx->sm_count * 4;
+  const int cs = ctx->tsel, ns = cs ^ 1;
+  // views over table set cs (this step's grid) and ns (the next step's)
+  ck::StepView vc = make_view(ctx);
+  ctx->tsel = ns;
+  ck::StepView vn = make_view(ctx);
+  ctx->tsel = cs;
+  ckmpm_ctx::EvPair ep{};
+  if (ctx->timing) cudaEventRecord(ctx->step_a, ctx->stream);
+  // every table set is cleared of the entries its last fill assigned (its
+  // list records them, slots claimed by the leftover P2G included) before it
+  // is filled again
+  ck::launch_table_reset(ctx->stream, vn.table, vn.g_list, vn.n_g, vn.pool_cap, grid_ctas);
+  if (!ctx->grid_valid) {
+    // prologue: binning, P2G and grid update of the current state into set cs
+    ck::launch_table_reset(ctx->stream, vc.table, vc.g_list, vc.n_g, vc.pool_cap, grid_ctas);
+    ck::launch_bin(ctx->stream, vc, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vc, bs, ck::LB_SCAN_TOP, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vc, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vc, bs, ck::LB_SCATTER, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vc, bs, ck::LB_GLIST, ngb, grid_ctas);
+    ck::launch_transfer(ctx->kind, ctx->lc, vc, ck::LK_P2G);
+    ck::launch_transfer(ctx->kind, ctx->lc, vc, ck::LK_UPDATE);
+    // the same particle blocks flag the next step's grid blocks
+    CK_TRY(cudaMemsetAsync(vn.n_g, 0, sizeof(uint32_t), ctx->stream), "memset");
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_GLIST, ngb, grid_ctas);
+    ctx->grid_valid = true;
+  } else {
+    tbeg(ctx, ep, 0);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_TOP, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 1);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCATTER, ngb, grid_ctas);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 5);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_GLIST, ngb, grid_ctas);
+    tend(ctx, ep);
+  }
+  // the fused kernel gathers through set cs and scatters through set ns
+  ck::StepView vf = vc;
+  vf.table_nxt = vn.table;
+  vf.g_list_nxt = vn.g_list;
+  vf.g_scene_nxt = vn.g_scene;
+  vf.n_g_nxt = vn.n_g;
+  tbeg(ctx, ep, 7);
+  ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_G2P2G);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 6);
+  ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_G2P_FP64);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 2);
+  ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_LEFTOVER);
+  tend(ctx, ep);
+  tbeg(ctx, ep, 3);
+  ck::launch_transfer(ctx->kind, ctx->lc, vn, ck::LK_UPDATE);
+  tend(ctx, ep);
+  if (ctx->timing) cudaEventRecord(ctx->step_b, ctx->stream);
+  CK_TRY(cudaGetLastError(), "step launch");
+  ctx->cur ^= 1;
+  ctx->tsel = ns;
   ctx->n_cur = n_live;
   rebuild_layout_sorted(ctx);
   ctx->steps++;
@@ -736,6 +868,7 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
     dev_free(ctx, dE);
   }
   ctx->layout.push_back({slot, ctx->n_cur, sc->n});
+  ctx->grid_valid = false;
   ctx->n_cur += sc->n;
   if (scene_id) *scene_id = slot;
   return CKMPM_OK;
@@ -838,6 +971,7 @@ ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id) {
   CK_TRY(cudaMemsetAsync(ctx->bnd[ctx->cur] + 2 * h.key_base, 0, sizeof(uint32_t) * 2 * h.nkeys, ctx->stream),
          "memset");
   h.alive = false;
+  ctx->grid_valid = false;
   ctx->h_scenes[scene_id].alive = 0;
   CK_TRY(cudaMemcpyAsync(ctx->d_scenes + scene_id, &ctx->h_scenes[scene_id], sizeof(SceneDev), cudaMemcpyHostToDevice,
                          ctx->stream),
@@ -896,6 +1030,15 @@ ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, 
     want = sizeof(float) * (size_t)(f * h.n);
   }
   if (bytes != want) return fail(ctx, CKMPM_EINVAL, "readback size mismatch: expected " + std::to_string(want));
+  // a fused step leaves the next step's grid as velocities and masses only
+  // (its grid update consumed the momenta): mass and velocity come from
+  // there until a probe replaces them
+  int which = field - CKMPM_FIELD_GRID_M;
+  if (field >= CKMPM_FIELD_GRID_M && ctx->fused && ctx->grid_valid) {
+    if (field == CKMPM_FIELD_GRID_P)
+      return fail(ctx, CKMPM_EINVAL, "after a fused step the grid momentum is consumed; probe the grids for it");
+    which = field == CKMPM_FIELD_GRID_M ? 3 : 4;
+  }
   float* out = (float*)dst;
   void* tmp = nullptr;
   if (!dst_is_device) {
@@ -909,7 +1052,7 @@ ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, 
       if (tmp) dev_free(ctx, tmp);
       return cuda_fail(ctx, me, "memset");
     }
-    ck::launch_read_grid(ctx->kind, ctx->stream, make_view(ctx), scene_id, field - CKMPM_FIELD_GRID_M, out);
+    ck::launch_read_grid(ctx->kind, ctx->stream, make_view(ctx), scene_id, which, out);
   } else {
     const Seg* sg = find_seg(ctx, scene_id);
     if (!sg) {
@@ -966,12 +1109,13 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
 ckmpm_status ckmpm_get_stats(ckmpm_ctx* ctx, ckmpm_stats* out) {
   if (!ctx || !out) return CKMPM_EINVAL;
   CK_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
-  uint32_t c[8];
+  uint32_t c[12];
   CK_TRY(cudaMemcpy(c, ctx->counters, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
   std::memset(out, 0, sizeof(*out));
   out->n_particles = ctx->n_cur;
   out->n_particle_blocks = c[0];
-  out->n_grid_blocks = c[1];
+  out->n_grid_blocks = c[ctx->tsel == 0 ? 1 : 8];
+  out->leftover_particles = ctx->fused ? c[9] : 0;
   out->steps = ctx->steps;
   unsigned long long f64 = 0;
   std::memcpy(&f64, &c[4], sizeof(f64));
@@ -987,7 +1131,7 @@ ckmpm_status ckmpm_get_stats(ckmpm_ctx* ctx, ckmpm_stats* out) {
     out->ms_kernel[i] = ctx->ms_cnt[i] ? ctx->ms_sum[i] / ctx->ms_cnt[i] : 0.0;
     out->launches_kernel[i] = ctx->ms_cnt[i];
   }
-  out->launches_per_step = 9;
+  out->launches_per_step = ctx->fused ? 11 : 9;
   return CKMPM_OK;
 }
 

@@ -17,7 +17,7 @@ struct LaunchCfg {
   int p2g_rep = 1;      // copies of the P2G shared accumulators (1 or 2)
 };
 
-enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4 };
+enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4, LK_G2P2G = 5, LK_LEFTOVER = 6 };
 
 // transfer.cu
 void launch_transfer(int kind, const LaunchCfg& lc, const StepView& v, int which);
@@ -45,5 +45,7 @@ void launch_bin(cudaStream_t st, const StepView& v, const BinScratch& bs, int wh
                 int grid_ctas);
 enum { LB_SCAN_TILES = 0, LB_SCAN_TOP = 1, LB_SCAN_FINAL = 2, LB_SCATTER = 3, LB_GLIST = 4 };
 void launch_mark_dead(cudaStream_t st, uint32_t* key, uint32_t start, uint32_t n);
+void launch_table_reset(cudaStream_t st, uint32_t* table, const uint32_t* g_list, const uint32_t* n_g,
+                        uint32_t pool_cap, int grid_ctas);
 
 }  // namespace ck

@@ -841,6 +841,179 @@ __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(
 constexpr int kG2PWarp = 32;
 __host__ __device__ constexpr int g2p_stage(int minb) { return minb >= 5 ? 64 : 128; }  // particles per chunk
 
+// Result of one particle's G2P: its next key and P2G contribution bounds,
+// whether its constitutive update was deferred to the float64 pass, and
+// whether its new state is finite.
+struct G2POut {
+  uint32_t nk;
+  float bmass, bmom;
+  bool use64, fin;
+};
+
+// G2P of one particle (slot t of the current binned order): gather v and B
+// (or the kernel-gradient sums) from the staged grid velocities sv, F update,
+// constitutive update (or listing for the float64 pass), advection, next key
+// and bounds; stores the new state at slot t of nxt.  Returns false (and
+// flags CK_ERR_INTERNAL) for a particle outside its block.
+template <int KIND, int TR>
+__device__ __forceinline__ bool g2p_particle(const StepView& v, const SceneDev& s, int ox, int oy, int oz,
+                                             const float4* sv, uint32_t t, const float4 X, const float4 f0,
+                                             const float4 f1, const float f2, const uint32_t id, const float Eraw,
+                                             G2POut& out) {
+  out.use64 = false;
+  const uint32_t mi = __float_as_uint(X.w);
+  const MatDev mt = v.mats[mi];
+  float mu = mt.mu, lam = mt.lam;
+  float Ep = 0.f;
+  if (v.cur.E) {
+    Ep = Eraw;
+    mu = Ep / (2.0f * (1.0f + mt.nu));
+    lam = Ep * mt.nu / ((1.0f + mt.nu) * (1.0f - 2.0f * mt.nu));
+  }
+  Sten<KIND> st;
+  if (!st.set(X.x * s.inv_dx, X.y * s.inv_dx, X.z * s.inv_dx, ox, oy, oz)) {
+    flag_error(v.err, CK_ERR_INTERNAL);
+    return false;
+  }
+  float vel[3], Bh[9], G[9];
+  if constexpr (TR == 1) {
+    // grad v = -Gr / dx (Gr in Bh); F' = (I + dt grad v) F
+    st.set_grad();
+    g2p_gather_grad(st, sv, vel, Bh);
+    const float sc = -s.dt * s.inv_dx;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) G[q] = sc * Bh[q];
+  } else if constexpr (TR == 2) {
+    // B from the APIC moments, grad v = -Gr / dx from the derivative sums
+    g2p_gather(st, sv, vel, Bh);
+    st.set_grad();
+    float vg[3];
+    g2p_gather_grad(st, sv, vg, G);
+    const float sc = -s.dt * s.inv_dx;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) G[q] *= sc;
+  } else {
+    // C = B D^-1 = Bh D^-1 / dx ; F' = (I + dt C) F
+    g2p_gather(st, sv, vel, Bh);
+    mul_dinv(st, Bh, s.dt * s.inv_dx, G);
+  }
+  const float vx = vel[0], vy = vel[1], vz = vel[2];
+  G[0] += 1.0f;
+  G[4] += 1.0f;
+  G[8] += 1.0f;
+  const float Fo[9] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2};
+  float F[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      F[r * 3 + q] = G[r * 3 + 0] * Fo[0 * 3 + q] + G[r * 3 + 1] * Fo[1 * 3 + q] + G[r * 3 + 2] * Fo[2 * 3 + q];
+  // constitutive update in float32 from the left stretch; degenerate or
+  // inverted F is deferred to the float64 pass (precision extension):
+  // this kernel stores F' and M = m B' (no stress) and lists the particle
+  float tau[9];
+  // Drucker-Prager at small stretch: matrix log/exp series, no eigen-
+  // decomposition (such F is far from every float64 criterion)
+  float Xs[6];
+  const bool small_dp = mt.model == 1 && s.gap_tol <= 0.f && s.j_tol < 0.9f && s.cond_tol < 0.9f &&
+                        left_strain(F, Xs) <= (1.f / 48.f);
+  if (mt.model == 2) {
+    // J-based fluid: volume ratio only, stress from J (no decomposition)
+    fluid_update<float>(F, mt.E, mt.gamma, tau);
+  } else if (small_dp) {
+    dp_small_strain(F, Xs, mu, lam, mt.dpc, tau);
+  } else {
+    // b = F F^T = U diag(sigma^2) U^T
+    float bq[9], U[9], e[3], sg[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = r; q < 3; ++q) {
+        const float d = F[r * 3] * F[q * 3] + F[r * 3 + 1] * F[q * 3 + 1] + F[r * 3 + 2] * F[q * 3 + 2];
+        bq[r * 3 + q] = d;
+        bq[q * 3 + r] = d;
+      }
+    sym_eig3<float>(bq, U, e);
+    sg[0] = sqrtf(fmaxf(e[0], 0.f));
+    sg[1] = sqrtf(fmaxf(e[1], 0.f));
+    sg[2] = sqrtf(fmaxf(e[2], 0.f));
+    const float J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                    F[2] * (F[3] * F[7] - F[4] * F[6]);
+    const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
+    const float smin = min3(sg[0], sg[1], sg[2]);
+    const float gap = min3(fabsf(sg[0] - sg[1]), fabsf(sg[0] - sg[2]), fabsf(sg[1] - sg[2]));
+    const bool use64 = !(J > 0.f) || (fabsf(J) < s.j_tol) || (smin < s.cond_tol * smax) ||
+                       (gap < s.gap_tol * smax);
+    out.use64 = use64;
+    if (use64) {
+      const unsigned long long slot = atomicAdd(v.fp64_count, 1ull);
+      v.fp64_list[slot] = t;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) tau[q] = 0.f;
+    } else {
+      constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, U, e, sg);
+    }
+  }
+  // M' = m B' - dt V0 tau, B' = dx Bh (APIC) or 0 (PIC); the kernel-
+  // gradient APIC keeps M' = m B' and T' = -dt V0 tau apart
+  const float mdx = mt.mass * s.dx, dtv = s.dt * s.V0;
+  float Mn[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    Mn[q] = TR == 1 ? -dtv * tau[q] : TR == 2 ? mdx * Bh[q] : mdx * Bh[q] - dtv * tau[q];
+  float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
+  // next key; particles leaving the interior are clamped and flagged
+  float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
+  // x was finite, so x + dt v is finite when v is
+  bool fin = isfinite(vx) && isfinite(vy) && isfinite(vz);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]) && (TR != 2 || isfinite(tau[q]));
+  if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
+  out.fin = fin;
+  if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {
+    flag_error(v.err, CK_ERR_DOMAIN);
+    const float lo = 0.5f, hi = (float)s.res - 0.5f - 1e-3f;
+    ux = fminf(fmaxf(isfinite(ux) ? ux : lo, lo), hi);
+    uy = fminf(fmaxf(isfinite(uy) ? uy : lo, lo), hi);
+    uz = fminf(fmaxf(isfinite(uz) ? uz : lo, lo), hi);
+    Xn.x = ux * s.dx;
+    Xn.y = uy * s.dx;
+    Xn.z = uz * s.dx;
+    ux = Xn.x * s.inv_dx;
+    uy = Xn.y * s.inv_dx;
+    uz = Xn.z * s.inv_dx;
+  }
+  const uint32_t nk = particle_key<KIND>(s, ux, uy, uz);
+  v.nxt.X[t] = Xn;
+  v.nxt.VM0[t] = make_float4(vx, vy, vz, Mn[0]);
+  v.nxt.VM1[t] = make_float4(Mn[1], Mn[2], Mn[3], Mn[4]);
+  v.nxt.VM2[t] = make_float4(Mn[5], Mn[6], Mn[7], Mn[8]);
+  v.nxt.F0[t] = make_float4(F[0], F[1], F[2], F[3]);
+  v.nxt.F1[t] = make_float4(F[4], F[5], F[6], F[7]);
+  v.nxt.F2[t] = F[8];
+  v.nxt.ID[t] = id;
+  if (v.nxt.E) v.nxt.E[t] = Ep;
+  v.key_nxt[t] = nk;
+  out.nk = nk;
+  float& bmass = out.bmass;
+  float& bmom = out.bmom;
+  if constexpr (TR == 2) {
+    float Tn[9], Mb[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      Tn[q] = -dtv * tau[q];
+      Mb[q] = fabsf(Mn[q]) + fabsf(Tn[q]);
+    }
+    v.nxt.T0[t] = make_float4(Tn[0], Tn[1], Tn[2], Tn[3]);
+    v.nxt.T1[t] = make_float4(Tn[4], Tn[5], Tn[6], Tn[7]);
+    v.nxt.T2[t] = Tn[8];
+    p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mb, bmass, bmom);
+  } else {
+    p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mn, bmass, bmom);
+  }
+  return true;
+}
+
 // TR: transfer, 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient.
 template <int KIND, int MINB, int TR>
 __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
@@ -895,165 +1068,270 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
     cp_async_wait_all();
     __syncwarp();
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const uint32_t t = start + c0 + i;
-      const float4 X = sX[i];
-      const float4 f0 = sF0[i];
-      const float4 f1 = sF1[i];
-      const float f2 = sF2[i];
-      const uint32_t id = sID[i];
-      const uint32_t mi = __float_as_uint(X.w);
-      const MatDev mt = v.mats[mi];
-      float mu = mt.mu, lam = mt.lam;
-      float Ep = 0.f;
-      if (v.cur.E) {
-        Ep = sE[i];
-        mu = Ep / (2.0f * (1.0f + mt.nu));
-        lam = Ep * mt.nu / ((1.0f + mt.nu) * (1.0f - 2.0f * mt.nu));
-      }
-      Sten<KIND> st;
-      if (!st.set(X.x * s.inv_dx, X.y * s.inv_dx, X.z * s.inv_dx, ox, oy, oz)) {
-        flag_error(v.err, CK_ERR_INTERNAL);
-        continue;
-      }
-      float vel[3], Bh[9], G[9];
-      if constexpr (TR == 1) {
-        // grad v = -Gr / dx (Gr in Bh); F' = (I + dt grad v) F
-        st.set_grad();
-        g2p_gather_grad(st, sv, vel, Bh);
-        const float sc = -s.dt * s.inv_dx;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) G[q] = sc * Bh[q];
-      } else if constexpr (TR == 2) {
-        // B from the APIC moments, grad v = -Gr / dx from the derivative sums
-        g2p_gather(st, sv, vel, Bh);
-        st.set_grad();
-        float vg[3];
-        g2p_gather_grad(st, sv, vg, G);
-        const float sc = -s.dt * s.inv_dx;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) G[q] *= sc;
-      } else {
-        // C = B D^-1 = Bh D^-1 / dx ; F' = (I + dt C) F
-        g2p_gather(st, sv, vel, Bh);
-        mul_dinv(st, Bh, s.dt * s.inv_dx, G);
-      }
-      const float vx = vel[0], vy = vel[1], vz = vel[2];
-      G[0] += 1.0f;
-      G[4] += 1.0f;
-      G[8] += 1.0f;
-      const float Fo[9] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2};
-      float F[9];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          F[r * 3 + q] = G[r * 3 + 0] * Fo[0 * 3 + q] + G[r * 3 + 1] * Fo[1 * 3 + q] + G[r * 3 + 2] * Fo[2 * 3 + q];
-      // constitutive update in float32 from the left stretch; degenerate or
-      // inverted F is deferred to the float64 pass (precision extension):
-      // this kernel stores F' and M = m B' (no stress) and lists the particle
-      float tau[9];
-      // Drucker-Prager at small stretch: matrix log/exp series, no eigen-
-      // decomposition (such F is far from every float64 criterion)
-      float Xs[6];
-      const bool small_dp = mt.model == 1 && s.gap_tol <= 0.f && s.j_tol < 0.9f && s.cond_tol < 0.9f &&
-                            left_strain(F, Xs) <= (1.f / 48.f);
-      if (mt.model == 2) {
-        // J-based fluid: volume ratio only, stress from J (no decomposition)
-        fluid_update<float>(F, mt.E, mt.gamma, tau);
-      } else if (small_dp) {
-        dp_small_strain(F, Xs, mu, lam, mt.dpc, tau);
-      } else {
-        // b = F F^T = U diag(sigma^2) U^T
-        float bq[9], U[9], e[3], sg[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-          for (int q = r; q < 3; ++q) {
-            const float d = F[r * 3] * F[q * 3] + F[r * 3 + 1] * F[q * 3 + 1] + F[r * 3 + 2] * F[q * 3 + 2];
-            bq[r * 3 + q] = d;
-            bq[q * 3 + r] = d;
-          }
-        sym_eig3<float>(bq, U, e);
-        sg[0] = sqrtf(fmaxf(e[0], 0.f));
-        sg[1] = sqrtf(fmaxf(e[1], 0.f));
-        sg[2] = sqrtf(fmaxf(e[2], 0.f));
-        const float J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
-                        F[2] * (F[3] * F[7] - F[4] * F[6]);
-        const float smax = fmaxf(sg[0], fmaxf(sg[1], sg[2]));
-        const float smin = min3(sg[0], sg[1], sg[2]);
-        const float gap = min3(fabsf(sg[0] - sg[1]), fabsf(sg[0] - sg[2]), fabsf(sg[1] - sg[2]));
-        const bool use64 = !(J > 0.f) || (fabsf(J) < s.j_tol) || (smin < s.cond_tol * smax) ||
-                           (gap < s.gap_tol * smax);
-        if (use64) {
-          const unsigned long long slot = atomicAdd(v.fp64_count, 1ull);
-          v.fp64_list[slot] = t;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) tau[q] = 0.f;
-        } else {
-          constitutive_left<float>(mt.model, F, mu, lam, mt.alpha, tau, U, e, sg);
-        }
-      }
-      // M' = m B' - dt V0 tau, B' = dx Bh (APIC) or 0 (PIC); the kernel-
-      // gradient APIC keeps M' = m B' and T' = -dt V0 tau apart
-      const float mdx = mt.mass * s.dx, dtv = s.dt * s.V0;
-      float Mn[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q)
-        Mn[q] = TR == 1 ? -dtv * tau[q] : TR == 2 ? mdx * Bh[q] : mdx * Bh[q] - dtv * tau[q];
-      float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
-      // next key; particles leaving the interior are clamped and flagged
-      float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
-      // x was finite, so x + dt v is finite when v is
-      bool fin = isfinite(vx) && isfinite(vy) && isfinite(vz);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]) && (TR != 2 || isfinite(tau[q]));
-      if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
-      if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {
-        flag_error(v.err, CK_ERR_DOMAIN);
-        const float lo = 0.5f, hi = (float)s.res - 0.5f - 1e-3f;
-        ux = fminf(fmaxf(isfinite(ux) ? ux : lo, lo), hi);
-        uy = fminf(fmaxf(isfinite(uy) ? uy : lo, lo), hi);
-        uz = fminf(fmaxf(isfinite(uz) ? uz : lo, lo), hi);
-        Xn.x = ux * s.dx;
-        Xn.y = uy * s.dx;
-        Xn.z = uz * s.dx;
-        ux = Xn.x * s.inv_dx;
-        uy = Xn.y * s.inv_dx;
-        uz = Xn.z * s.inv_dx;
-      }
-      const uint32_t nk = particle_key<KIND>(s, ux, uy, uz);
-      v.nxt.X[t] = Xn;
-      v.nxt.VM0[t] = make_float4(vx, vy, vz, Mn[0]);
-      v.nxt.VM1[t] = make_float4(Mn[1], Mn[2], Mn[3], Mn[4]);
-      v.nxt.VM2[t] = make_float4(Mn[5], Mn[6], Mn[7], Mn[8]);
-      v.nxt.F0[t] = make_float4(F[0], F[1], F[2], F[3]);
-      v.nxt.F1[t] = make_float4(F[4], F[5], F[6], F[7]);
-      v.nxt.F2[t] = F[8];
-      v.nxt.ID[t] = id;
-      if (v.nxt.E) v.nxt.E[t] = Ep;
-      v.key_nxt[t] = nk;
-      float bmass, bmom;
-      if constexpr (TR == 2) {
-        float Tn[9], Mb[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          Tn[q] = -dtv * tau[q];
-          Mb[q] = fabsf(Mn[q]) + fabsf(Tn[q]);
-        }
-        v.nxt.T0[t] = make_float4(Tn[0], Tn[1], Tn[2], Tn[3]);
-        v.nxt.T1[t] = make_float4(Tn[4], Tn[5], Tn[6], Tn[7]);
-        v.nxt.T2[t] = Tn[8];
-        p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mb, bmass, bmom);
-      } else {
-        p2g_bounds<KIND>(s.inv_dx, mt.mass, vx, vy, vz, Mn, bmass, bmom);
-      }
-      warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, nk, bmass, bmom);
+      G2POut o;
+      if (g2p_particle<KIND, TR>(v, s, ox, oy, oz, sv, start + c0 + i, sX[i], sF0[i], sF1[i], sF2[i], sID[i],
+                                 v.cur.E ? sE[i] : 0.f, o))
+        warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, o.nk, o.bmass, o.bmom);
     }
     __syncwarp();  // the next chunk (or block) overwrites the staged copies
     }
     // last use of the block's count this step: clear it, so that this buffer
     // is all zero when G2P fills it as the next histogram
     if (threadIdx.x == 0) v.cnt_cur[key] = 0u;
+  }
+}
+
+// ------------------------------------------------------------ fused G2P2G
+//
+// The paper's G2P2G (Sec. 5.1, after Wang 2020) gathers step n and scatters
+// step n + 1 in one kernel.  Here one CTA (one warp) takes a particle block
+// of step n and
+//   1. runs G2P on every particle of the block exactly as k_g2p does
+//      (new state, next key, histogram and bounds for the next binning);
+//   2. scatters the particles that stay in the block (same key, float32
+//      constitutive update, finite) into the block's staged nodes with the
+//      fixed-point shared atomics of k_p2g, and flushes them into the next
+//      step's grid through its block table.
+// The fixed-point scale needs the bound of the block's new contributions
+// before the first atomic, so the scatter is a second pass that reads the
+// new state the first pass just wrote (contiguous, from L2), instead of a
+// stash in shared memory that would cost occupancy.  Particles that moved to
+// another block, took the float64 pass or became non-finite go to a list
+// that k_p2g_leftover scatters after the float64 pass.
+// The staged grid velocities of pass 1 and the accumulators of pass 2 share
+// one shared-memory arena.
+constexpr int kFuseMaxCnt = 4096;  // block particle count up to which stays are tracked (larger: all leftover)
+
+template <int KIND, int MINB>
+struct FuseSmem {
+  static constexpr int NS = Geo<KIND>::NS;
+  static constexpr int CAP = g2p_stage(MINB);
+  struct Ph1 {
+    float4 sv[NS];
+    float4 sX[CAP], sF0[CAP], sF1[CAP];
+    float sF2[CAP], sE[CAP];
+    uint32_t sID[CAP];
+  };
+  struct Ph2 {
+    int sm[4][NS];
+    float4 sX[kP2GStage], sA[kP2GStage], sB[kP2GStage], sC[kP2GStage];
+  };
+  static constexpr size_t bytes = sizeof(Ph1) > sizeof(Ph2) ? sizeof(Ph1) : sizeof(Ph2);
+};
+
+// Append value to a global list when pred holds (one atomic per warp).
+__device__ __forceinline__ void warp_append(uint32_t* count, uint32_t* list, uint32_t value, bool pred) {
+  const unsigned am = __activemask();
+  const unsigned m = __ballot_sync(am, pred);
+  if (!m) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(am, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+template <int KIND, int MINB>
+__global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
+  using SM = FuseSmem<KIND, MINB>;
+  constexpr int NS = SM::NS;
+  constexpr int CAP = SM::CAP;
+  constexpr uint32_t PCAP = kP2GStage, PC = kP2GStage / 32;
+  static_assert(CAP % 32 == 0, "the stay mask takes one ballot per 32 particles");
+  __shared__ __align__(16) unsigned char arena[SM::bytes];
+  __shared__ uint32_t stay[kFuseMaxCnt / 32];
+  __shared__ uint32_t bslot[8];
+  auto& p1 = *reinterpret_cast<typename SM::Ph1*>(arena);
+  auto& p2 = *reinterpret_cast<typename SM::Ph2*>(arena);
+  const uint32_t npb = *v.n_pb;
+  const uint32_t lane = threadIdx.x;
+  for (;;) {
+    uint32_t bi = 0;
+    if (lane == 0) bi = atomicAdd(&v.work[1], 1u);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    if (bi >= npb) break;
+    const uint32_t key = v.pb_key[bi];
+    const SceneDev s = v.scenes[v.pb_scene[bi]];
+    const uint32_t start = v.offset[key];
+    const uint32_t cnt = v.cnt_cur[key];
+    const bool track = cnt <= (uint32_t)kFuseMaxCnt;
+    int ox, oy, oz;
+    decode_block(s, key, ox, oy, oz);
+    load_block_slots(v, s, ox, oy, oz, bslot);  // this step's grid (gather)
+    __syncwarp();
+    // ---- pass 1: G2P of the block
+    float bm_max = 0.f, bp_max = 0.f;
+    uint32_t nstay = 0;
+    for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
+      const uint32_t m = min(cnt - c0, (uint32_t)CAP);
+#pragma unroll 4
+      for (uint32_t i = lane; i < m; i += 32) {
+        const uint32_t p = v.perm[start + c0 + i];
+        cp_async16(&p1.sX[i], &v.cur.X[p]);
+        cp_async16(&p1.sF0[i], &v.cur.F0[p]);
+        cp_async16(&p1.sF1[i], &v.cur.F1[p]);
+        cp_async4(&p1.sF2[i], &v.cur.F2[p]);
+        cp_async4(&p1.sID[i], &v.cur.ID[p]);
+        if (v.cur.E) cp_async4(&p1.sE[i], &v.cur.E[p]);
+      }
+      if (c0 == 0) {
+        for (int j = lane; j < NS; j += 32) {
+          int g, lx, ly, lz;
+          staged_coords<KIND>(j, g, lx, ly, lz);
+          long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
+          if (gi >= 0)
+            cp_async16(&p1.sv[j], &v.Gvel[gi]);
+          else
+            p1.sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      for (uint32_t i = lane; i < m; i += 32) {
+        const uint32_t t = start + c0 + i;
+        G2POut o;
+        const bool ok = g2p_particle<KIND, 0>(v, s, ox, oy, oz, p1.sv, t, p1.sX[i], p1.sF0[i], p1.sF1[i],
+                                              p1.sF2[i], p1.sID[i], v.cur.E ? p1.sE[i] : 0.f, o);
+        if (ok) warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, o.nk, o.bmass, o.bmom);
+        const bool st = ok && track && o.nk == key && !o.use64 && o.fin;
+        if (st) {
+          bm_max = fmaxf(bm_max, o.bmass);
+          bp_max = fmaxf(bp_max, o.bmom);
+          nstay += 1;
+        }
+        warp_append(v.lo_count, v.lo_list, t, ok && !st);
+        const unsigned am = __activemask();
+        const unsigned w = __ballot_sync(am, st);
+        if (track && (int)lane == __ffs(am) - 1) stay[(c0 + i - lane) >> 5] = w;
+      }
+      __syncwarp();  // the next chunk overwrites the staged copies
+    }
+    // ---- pass 2: P2G of the particles that stayed, into the next grid
+    bm_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(bm_max)));
+    bp_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(bp_max)));
+    nstay = __reduce_add_sync(0xffffffffu, nstay);
+    if (nstay > 0) {
+      if (lane < 8) {  // the next step's grid blocks (scatter)
+        const int bx = (ox >> 2) + (lane & 1), by = (oy >> 2) + ((lane >> 1) & 1), bz = (oz >> 2) + (lane >> 2);
+        bslot[lane] = v.table_nxt[s.table_base + ((long long)bz * s.nb + by) * s.nb + bx];
+      }
+      for (int j = lane; j < NS; j += 32) reinterpret_cast<int4*>(&p2.sm[0][0])[j] = make_int4(0, 0, 0, 0);
+      const float fst = (float)nstay;
+      const float Sm = bm_max > 0.f ? 1073741824.0f / (fst * bm_max) : 1.0f;
+      const float Sp = bp_max > 0.f ? 1073741824.0f / (fst * bp_max) : 1.0f;
+      for (uint32_t c0 = 0; c0 < cnt; c0 += PCAP) {
+        const uint32_t m = min(cnt - c0, PCAP);
+#pragma unroll
+        for (uint32_t r = 0; r < PC; ++r) {
+          const uint32_t i = lane + r * 32;
+          if (i < m) {
+            const uint32_t t = start + c0 + i;
+            cp_async16(&p2.sX[i], &v.nxt.X[t]);
+            cp_async16(&p2.sA[i], &v.nxt.VM0[t]);
+            cp_async16(&p2.sB[i], &v.nxt.VM1[t]);
+            cp_async16(&p2.sC[i], &v.nxt.VM2[t]);
+          }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll 1
+        for (uint32_t r = 0; r < PC; ++r) {
+          const uint32_t i = lane * PC + r;
+          const uint32_t q = c0 + i;
+          if (i < m && ((stay[q >> 5] >> (q & 31)) & 1u)) {
+            const P2GPart part{p2.sX[i], p2.sA[i], p2.sB[i], p2.sC[i]};
+            p2g_scatter<KIND>(s, v.mats, v.err, part, ox, oy, oz, Sm, Sp, p2.sm);
+          }
+        }
+        __syncwarp();
+      }
+      const float iSm = 1.0f / Sm, iSp = 1.0f / Sp;
+      for (int j = lane; j < NS; j += 32) {
+        const int mi = p2.sm[0][j];
+        if (mi != 0) {
+          int g, lx, ly, lz;
+          staged_coords<KIND>(j, g, lx, ly, lz);
+          const long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
+          if (gi >= 0)
+            atomicAdd(&v.Gacc[gi], make_float4((float)mi * iSm, (float)p2.sm[1][j] * iSp,
+                                               (float)p2.sm[2][j] * iSp, (float)p2.sm[3][j] * iSp));
+          else
+            flag_error(v.err, CK_ERR_POOL);
+        }
+      }
+    }
+    // last use of the block's count and bounds this step
+    if (lane == 0) {
+      v.cnt_cur[key] = 0u;
+      v.bnd_cur[2 * key] = 0u;
+      v.bnd_cur[2 * key + 1] = 0u;
+    }
+    __syncwarp();  // the next block reuses the arena and the slots
+  }
+}
+
+// Pool slot of virtual grid block g in the next step's table; a block no
+// fused scatter touched is claimed here: a slot is taken from the counter
+// and offered to the table with one compare-and-swap; when another thread
+// got there first its slot is used and this one stays empty (its
+// accumulators are zero, so the grid update leaves it at rest).  No thread
+// waits on another.
+__device__ __forceinline__ uint32_t claim_slot(const StepView& v, long long g, uint32_t scene) {
+  const uint32_t cur = v.table_nxt[g];
+  if (cur != CK_NO_SLOT) return cur;
+  const uint32_t ns = atomicAdd(v.n_g_nxt, 1u);
+  if (ns >= v.pool_cap) {
+    flag_error(v.err, CK_ERR_POOL);
+    return CK_NO_SLOT;
+  }
+  v.g_list_nxt[ns] = (uint32_t)g;
+  v.g_scene_nxt[ns] = scene;
+  const uint32_t old = atomicCAS(&v.table_nxt[g], CK_NO_SLOT, ns);
+  return old == CK_NO_SLOT ? ns : old;
+}
+
+// P2G of the particles the fused kernel left over (new state in nxt, after
+// the float64 pass): one particle per thread, contributions in float added
+// with one 16-byte global atomic per node (APIC + MLS; quadratic or CK).
+template <int KIND>
+__global__ void __launch_bounds__(128) k_p2g_leftover(StepView v) {
+  constexpr int NG = Geo<KIND>::NG;
+  const uint32_t n = min(*v.lo_count, v.n_cur);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = v.lo_list[i];
+    const float4 X = v.nxt.X[t];
+    const MatDev mt = v.mats[__float_as_uint(X.w)];
+    const SceneDev s = v.scenes[mt.scene];
+    const float ux = X.x * s.inv_dx, uy = X.y * s.inv_dx, uz = X.z * s.inv_dx;
+    Cell<KIND> cx, cy, cz;
+    cx.set(ux);
+    cy.set(uy);
+    cz.set(uz);
+    const int ox = cx.block() * 4, oy = cy.block() * 4, oz = cz.block() * 4;
+    Sten<KIND> st;
+    if (!st.set(ux, uy, uz, ox, oy, oz)) {
+      flag_error(v.err, CK_ERR_INTERNAL);
+      continue;
+    }
+    float M[9];
+    const float4 a = v.nxt.VM0[t], b = v.nxt.VM1[t], c = v.nxt.VM2[t];
+    M[0] = a.w; M[1] = b.x; M[2] = b.y; M[3] = b.z; M[4] = b.w; M[5] = c.x; M[6] = c.y; M[7] = c.z; M[8] = c.w;
+    float A[9];
+    mul_dinv(st, M, s.inv_dx, A);
+    const float mass = mt.mass;
+    const float px = mass * a.x, py = mass * a.y, pz = mass * a.z;
+    for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
+      int g, lx, ly, lz;
+      staged_coords<KIND>(j, g, lx, ly, lz);
+      const int ix = ox + lx, iy = oy + ly, iz = oz + lz;
+      const long long gb = s.table_base + ((long long)(iz >> 2) * s.nb + (iy >> 2)) * s.nb + (ix >> 2);
+      const uint32_t sl = claim_slot(v, gb, mt.scene);
+      if (sl == CK_NO_SLOT) return;
+      const int l = ((iz & 3) * 4 + (iy & 3)) * 4 + (ix & 3);
+      atomicAdd(&v.Gacc[((long long)sl * NG + g) * kBlockNodes + l],
+                make_float4(w * mass, w * (px + A[0] * dx + A[1] * dy + A[2] * dz),
+                            w * (py + A[3] * dx + A[4] * dy + A[5] * dz), w * (pz + A[6] * dx + A[7] * dy + A[8] * dz)));
+    });
   }
 }
 
@@ -1293,7 +1571,10 @@ __global__ void k_write_particles(Pool P, const SceneDev* scenes, const MatDev* 
 
 // Dense grid fields of one scene: out[grid][iz][iy][ix] (x fastest) over
 // 0..res per axis, written from the active blocks of the last step (the
-// caller zeroes out first); which: 0 mass, 1 momentum (3), 2 velocity (3).
+// caller zeroes out first); which: 0 mass, 1 momentum (3), 2 velocity (3)
+// from a probe's accumulators; 3 mass, 4 velocity (3) from the grid a fused
+// step left (velocity and mass after its update), nodes with mass only, so
+// that a slot the leftover P2G claimed in vain (empty) writes nothing.
 template <int KIND>
 __global__ void k_read_grid(const float4* Gacc, const float4* Gvel, const uint32_t* g_list, const uint32_t* g_scene,
                             const uint32_t* n_g, uint32_t pool_cap, const SceneDev* scenes, int scene, int which,
@@ -1313,6 +1594,17 @@ __global__ void k_read_grid(const float4* Gacc, const float4* Gvel, const uint32
       if (ix >= n || iy >= n || iz >= n) continue;
       long long q = grid * nnode + ((long long)iz * n + iy) * n + ix;
       long long idx = ((long long)gi * NG + grid) * kBlockNodes + l;
+      if (which >= 3) {
+        const float4 g = Gvel[idx];
+        if (g.w > 0.f) {
+          if (which == 3) {
+            out[q] = g.w;
+          } else {
+            out[3 * q] = g.x; out[3 * q + 1] = g.y; out[3 * q + 2] = g.z;
+          }
+        }
+        continue;
+      }
       float4 a = Gacc[idx];
       if (which == 0) {
         out[q] = a.x;
@@ -1458,6 +1750,14 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
         k_g2p<KIND, 4, 0><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
       break;
     case LK_G2P_FP64: k_g2p_fp64<KIND><<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
+    // fused step (APIC + MLS): one resident wave at the G2P register budget
+    case LK_G2P2G:
+      if constexpr (KIND == 0)
+        k_g2p2g<KIND, 5><<<lc.sm_count * 20, kG2PWarp, 0, lc.stream>>>(v);
+      else
+        k_g2p2g<KIND, 4><<<lc.sm_count * 16, kG2PWarp, 0, lc.stream>>>(v);
+      break;
+    case LK_LEFTOVER: k_p2g_leftover<KIND><<<lc.sm_count * 4, 128, 0, lc.stream>>>(v); break;
     case LK_CLEAR: k_clear_gacc<KIND><<<lc.persistent_ctas, 128, 0, lc.stream>>>(v); break;
   }
 }

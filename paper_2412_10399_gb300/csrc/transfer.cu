@@ -964,10 +964,16 @@ __device__ __forceinline__ bool g2p_particle(const StepView& v, const SceneDev& 
   float4 Xn = make_float4(X.x + s.dt * vx, X.y + s.dt * vy, X.z + s.dt * vz, X.w);
   // next key; particles leaving the interior are clamped and flagged
   float ux = Xn.x * s.inv_dx, uy = Xn.y * s.inv_dx, uz = Xn.z * s.inv_dx;
-  // x was finite, so x + dt v is finite when v is
-  bool fin = isfinite(vx) && isfinite(vy) && isfinite(vz);
+  // x was finite, so x + dt v is finite when v is.  x * 0 is 0 for a finite
+  // x and NaN for an infinite or NaN one, so one sum of such products tests
+  // every value at one fused multiply-add each
+  float z = fmaf(vx, 0.f, fmaf(vy, 0.f, vz * 0.f));
 #pragma unroll
-  for (int q = 0; q < 9; ++q) fin = fin && isfinite(F[q]) && isfinite(Mn[q]) && (TR != 2 || isfinite(tau[q]));
+  for (int q = 0; q < 9; ++q) {
+    z = fmaf(F[q], 0.f, fmaf(Mn[q], 0.f, z));
+    if constexpr (TR == 2) z = fmaf(tau[q], 0.f, z);
+  }
+  const bool fin = z == 0.f;
   if (!fin) flag_error(v.err, CK_ERR_NONFINITE);
   out.fin = fin;
   if (!(in_domain(ux, s.res) && in_domain(uy, s.res) && in_domain(uz, s.res))) {

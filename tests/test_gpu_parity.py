@@ -382,3 +382,75 @@ def test_empty_scene_is_rejected():
     with pytest.raises(ck.CKMPMError) as ei:
         ck.ckmpm_create(sc, 0, 0)
     assert ei.value.status == ck.EINVAL
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+@pytest.mark.parametrize("fused", [False, True])
+def test_nonfinite_state_reports_enonfinite(bad, fused):
+    """One particle's F carries a NaN or an infinity: the step's finite check
+    (one multiply-add by zero per value, NaN for any non-finite input) flags
+    it and the next sync reports ENONFINITE; every loop of the
+    decompositions is bounded, so the step itself completes."""
+    ck = need_gpu()
+    sc, B, F = random_scene(500, 16, 51, f_scale=0.05)
+    F = F.copy()
+    F[7, 1, 2] = bad
+    sim = ck.Simulation(sc, sc.kernel | (ck.STEP_G2P2G if fused else 0))
+    sim.write(ck.FIELD_F, F)
+    sim.step(1)
+    with pytest.raises(ck.CKMPMError) as ei:
+        sim.sync()
+    assert ei.value.status == ck.ENONFINITE
+    sim.close()
+
+
+def _rotation(g):
+    q = g.normal(size=4)
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+@pytest.mark.parametrize("model,s1,s3", [(S.FIXED_COROTATED, 1.1, 0.9), (S.DRUCKER_PRAGER, 0.95, 0.9)])
+def test_float32_error_on_clustered_singular_values(model, s1, s3):
+    """Precision extension without the gap criterion: F = U diag(s1, s1 (1 +
+    delta), s3) V^T with delta from 1e-7 to 1e-3 and random rotations, away
+    from F = I, goes through the float32 eigen path (its pair of singular
+    values is clustered, its eigenvectors ill-determined).  Every node is a
+    wall, so F reaches the constitutive update unchanged; the projected F
+    (Drucker-Prager) and the stress, through the next P2G's momentum (v = 0,
+    B = 0), are compared with the float64 oracle.  The measured errors are
+    printed; the bounds are the float32 bounds of the one-step tests."""
+    ck = need_gpu()
+    n, res = 2000, 16
+    sc, B, _ = random_scene(n, res, 71, model=model, gravity=(0.0, 0.0, 0.0), bc_cells=float(res), v_scale=0.0)
+    g = np.random.default_rng(72)
+    deltas = np.array([1e-7, 1e-6, 1e-5, 1e-4, 1e-3])
+    F = np.empty((n, 3, 3))
+    for p in range(n):
+        d = deltas[p % len(deltas)]
+        F[p] = _rotation(g) @ np.diag([s1, s1 * (1 + d), s3]) @ _rotation(g).T
+    F = f32(F)
+    sim = ck.Simulation(sc, sc.kernel)
+    sim.write(ck.FIELD_F, F)
+    sim.step(1)
+    sim.sync()
+    n64 = int(sim.stats().fp64_particles)
+    Fg = sim.read(ck.FIELD_F)
+    sim.probe_grids()
+    gp = sim.read(ck.FIELD_GRID_P)
+    sim.close()
+    assert n64 == 0  # the default criteria (J, condition) leave these to float32
+    prm = O.params_from_scene(sc)
+    st1 = O.step(oracle_state(sc, np.zeros_like(B), F), prm)
+    grids = O.p2g(st1, prm)
+    nn = res + 1
+    errF = rel(Fg, st1.F.numpy())
+    errP = max(rel(gp[gi], grids[k][1].numpy().reshape(nn, nn, nn, 3)) for gi, k in enumerate(O.grid_ids(0)))
+    per_delta = {float(d): float(np.abs(Fg[i::len(deltas)] - st1.F.numpy()[i::len(deltas)]).max())
+                 for i, d in enumerate(deltas)}
+    print(f"\nclustered sigma, model {model}: F rel err {errF:.3e}, stress-momentum rel err {errP:.3e}, "
+          f"max |dF| by delta {per_delta}")
+    assert errF <= 2e-6
+    assert errP <= 1e-5

@@ -2,17 +2,25 @@
 
 Requests (a scene and a number of steps) arrive over time.  All resident
 scenes advance together: every global step is one launch per kernel over the
-concatenated block lists of every scene in the context.  Between global steps
-the loop retires finished scenes (reading back their final state) and admits
-waiting requests, first come first served, as soon as the device-memory
-budget they need is free.  Each scene-step's latency is the device time of the
-global step it belonged to; p50 / p99 are reported beside the throughput.
+concatenated block lists of every scene in the context.  The loop does not
+wait for a global step: it enqueues the step with a pair of CUDA events
+around it and goes on admitting and retiring while the device runs, with at
+most ``max_inflight`` steps queued ahead; finished event pairs are harvested
+by polling.  Waiting requests are admitted first come first served as soon as
+the device-memory budget they need is free (admission is stream-ordered, so
+it takes effect at the next enqueued step); a scene whose last step has been
+enqueued is retired by reading back its final state, the one point where the
+host waits for the device.  Reported: the device time of the global step
+each scene-step belonged to (p50 / p99), and what a request sees: the wall
+time from its arrival to its result and its wall time per step while
+resident (p50 / p99), beside device-busy and wall throughput.
 
 The admission arithmetic is plain host code (``Budget``); the engine is any
 object with the ``admit / release / step / read`` methods of ``EngineCK``.
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 import math
 import time
@@ -100,6 +108,8 @@ class Result:
     finished_at_step: int
     queue_s: float
     fields: Dict[int, object]
+    admitted_s: float = 0.0   # wall time (from the server's start) of admission
+    finished_s: float = 0.0   # wall time at which the result was read back
 
 
 class EngineCK:
@@ -126,6 +136,7 @@ class EngineCK:
         cfg.stream = stream
         self.ctx = ck.ckmpm_create_server(cfg)
         self.kernel = kernel
+        self._events = []
 
     def admit(self, scene) -> int:
         sc, keep = self.ck.scene_struct(scene)
@@ -139,15 +150,34 @@ class EngineCK:
     def release(self, sid: int):
         self.ck.ckmpm_release(self.ctx, sid)
 
-    def step(self) -> float:
-        """One global step; returns its device time in ms."""
-        a = self.torch.cuda.Event(enable_timing=True)
-        b = self.torch.cuda.Event(enable_timing=True)
+    class _Pending:
+        """A global step in flight: its event pair, returned to the engine's
+        pool once its time has been read."""
+
+        def __init__(self, eng, a, b):
+            self.eng, self.a, self.b = eng, a, b
+
+        def done(self) -> bool:
+            return self.b.query()
+
+        def ms(self) -> float:
+            self.b.synchronize()
+            t = self.a.elapsed_time(self.b)
+            self.eng._events.append((self.a, self.b))
+            return t
+
+    def step_async(self) -> "EngineCK._Pending":
+        """Enqueue one global step between two CUDA events; does not wait."""
+        a, b = self._events.pop() if self._events else (self.torch.cuda.Event(enable_timing=True),
+                                                          self.torch.cuda.Event(enable_timing=True))
         a.record(self.stream)
         self.ck.ckmpm_step(self.ctx, 1)
         b.record(self.stream)
-        b.synchronize()
-        return a.elapsed_time(b)
+        return EngineCK._Pending(self, a, b)
+
+    def step(self) -> float:
+        """One global step; returns its device time in ms (waits for it)."""
+        return self.step_async().ms()
 
     def read(self, sid: int, field: int, n: int):
         import numpy as np
@@ -163,17 +193,21 @@ class EngineCK:
 
 
 class Server:
-    """Continuous-batching loop: FIFO admission under a resource budget."""
+    """Continuous-batching loop: FIFO admission under a resource budget,
+    global steps enqueued without waiting (at most max_inflight ahead)."""
 
-    def __init__(self, engine, budget: Budget, clock: Callable[[], float] = time.perf_counter):
+    def __init__(self, engine, budget: Budget, clock: Callable[[], float] = time.perf_counter,
+                 max_inflight: int = 8):
         self.engine = engine
         self.budget = budget
         self.clock = clock
+        self.max_inflight = max(1, max_inflight)
         self.waiting: List[Request] = []
         self.resident: Dict[int, dict] = {}
         self.used: Dict[str, int] = {}
         self.results: List[Result] = []
         self.latencies_ms: List[float] = []
+        self.inflight = collections.deque()  # (pending step, number of scenes it advanced)
         self.step_count = 0
         self.particle_steps = 0
         self.busy_ms = 0.0
@@ -199,8 +233,17 @@ class Server:
             for k, v in need.items():
                 self.used[k] = self.used.get(k, 0) + v
             self.resident[sid] = {"req": req, "left": req.steps, "need": need, "admitted": self.step_count,
-                                  "queue_s": max(0.0, now - req.arrival_s)}
+                                  "queue_s": max(0.0, now - req.arrival_s), "admitted_s": now}
             self.waiting.pop(0)
+
+    def _harvest(self, wait: bool = False):
+        """Account the device time of finished global steps (all of those in
+        flight with wait=True, else only those already done)."""
+        while self.inflight and (wait or self.inflight[0][0].done()):
+            pending, k = self.inflight.popleft()
+            ms = pending.ms()
+            self.busy_ms += ms
+            self.latencies_ms.extend([ms] * k)
 
     def _retire_finished(self):
         for sid in [s for s, r in self.resident.items() if r["left"] == 0]:
@@ -210,42 +253,60 @@ class Server:
             self.engine.release(sid)
             for k, v in r["need"].items():
                 self.used[k] -= v
-            self.results.append(Result(req, r["admitted"], self.step_count, r["queue_s"], fields))
+            self.results.append(Result(req, r["admitted"], self.step_count, r["queue_s"], fields,
+                                       admitted_s=r["admitted_s"], finished_s=self.clock() - self.t0))
 
     def poll(self) -> bool:
-        """Admit, run one global step if anything is resident, retire.  Returns
-        False once nothing is waiting or resident."""
+        """Harvest finished steps, admit, enqueue one global step if anything
+        is resident, retire.  Returns False once nothing is waiting, resident
+        or in flight."""
         now = self.clock() - self.t0
+        self._harvest()
         self._blocked = False
         self._admit_ready(now)
         if self._blocked and not self.resident:
-            self.engine.step()  # nothing resident: this step only compacts the pool
+            # nothing resident: one step only compacts the pool (the released
+            # scenes' particles leave it); the host's capacity count follows
+            self.engine.step_async().ms()
             self._admit_ready(now)
         if self.resident:
-            ms = self.engine.step()
+            if len(self.inflight) >= self.max_inflight:
+                pending, k = self.inflight.popleft()
+                ms = pending.ms()
+                self.busy_ms += ms
+                self.latencies_ms.extend([ms] * k)
+            self.inflight.append((self.engine.step_async(), len(self.resident)))
             self.step_count += 1
-            self.busy_ms += ms
             for r in self.resident.values():
                 r["left"] -= 1
-                self.latencies_ms.append(ms)
                 self.particle_steps += r["req"].scene.n
             self._retire_finished()
-        return bool(self.waiting or self.resident)
+        if not (self.waiting or self.resident):
+            self._harvest(wait=True)
+        return bool(self.waiting or self.resident or self.inflight)
 
     def run(self, sleep: Callable[[float], None] = time.sleep):
         while self.poll():
-            if not self.resident and self.waiting:
+            if not self.resident and self.waiting and not self.inflight:
                 wait = self.waiting[0].arrival_s - (self.clock() - self.t0)
                 if wait > 0:
                     sleep(min(wait, 0.01))
         return self.results
 
     def stats(self) -> dict:
-        lat = sorted(self.latencies_ms)
-        pick = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)] if lat else None
+        def pick(vals, q):
+            v = sorted(vals)
+            return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)] if v else None
+
         wall = self.clock() - self.t0
-        return {"p50_ms": pick(0.50), "p99_ms": pick(0.99), "scene_steps": len(lat),
+        e2e = [r.finished_s - r.request.arrival_s for r in self.results]
+        per_step = [1e3 * (r.finished_s - r.admitted_s) / max(1, r.request.steps) for r in self.results]
+        return {"p50_ms": pick(self.latencies_ms, 0.50), "p99_ms": pick(self.latencies_ms, 0.99),
+                "scene_steps": len(self.latencies_ms),
                 "global_steps": self.step_count, "scenes_finished": len(self.results),
                 "aggregate_particle_steps_per_s": self.particle_steps / (self.busy_ms / 1e3) if self.busy_ms else None,
                 "wall_particle_steps_per_s": self.particle_steps / wall if wall > 0 else None,
-                "mean_queue_s": (sum(r.queue_s for r in self.results) / len(self.results)) if self.results else None}
+                "mean_queue_s": (sum(r.queue_s for r in self.results) / len(self.results)) if self.results else None,
+                "request_latency_p50_s": pick(e2e, 0.50), "request_latency_p99_s": pick(e2e, 0.99),
+                "resident_wall_ms_per_step_p50": pick(per_step, 0.50),
+                "resident_wall_ms_per_step_p99": pick(per_step, 0.99)}

@@ -7,8 +7,27 @@ from paper_2412_10399_gb300 import scenes as S
 from paper_2412_10399_gb300 import serving as SV
 
 
+class FakePending:
+    """A step in flight: done after `lag` polls of done(); ms() waits for it."""
+
+    def __init__(self, eng, ms, lag=2):
+        self.eng, self._ms, self.left = eng, ms, lag
+        self.harvested = False
+
+    def done(self):
+        self.left -= 1
+        return self.left < 0
+
+    def ms(self):
+        self.eng.waits += 0 if self.left < 0 else 1
+        self.harvested = True
+        return self._ms
+
+
 class FakeEngine:
     def __init__(self):
+        self.pending = []
+        self.waits = 0
         self.next_id = 0
         self.resident = set()
         self.max_resident = 0
@@ -27,10 +46,12 @@ class FakeEngine:
     def release(self, sid):
         self.resident.remove(sid)
 
-    def step(self):
+    def step_async(self):
         for s in self.resident:
             self.steps_of[s] += 1
-        return 0.5 + 0.1 * len(self.resident)
+        p = FakePending(self, 0.5 + 0.1 * len(self.resident))
+        self.pending.append(p)
+        return p
 
     def read(self, sid, field, n):
         return np.full((n, 3), float(self.steps_of[sid]), np.float32)
@@ -106,3 +127,25 @@ def test_budget_from_bytes_stays_within_the_budget(kernel):
     assert b.particles > 10_000_000
     # every scene that fits alone fits the pool reservation
     assert b.fits({}, SV.scene_resources(2_000_000, 128))
+
+
+def test_steps_are_enqueued_without_waiting_and_bounded_in_flight():
+    """The loop enqueues global steps ahead of the device and waits only when
+    max_inflight steps are queued (or at the end): never more than that many
+    are un-harvested, every step's time is accounted once, and what a request
+    sees (arrival to result, wall time per resident step) is reported."""
+    eng = FakeEngine()
+    srv = SV.Server(eng, _budget_for(2, 1000), clock=FakeClock(), max_inflight=3)
+    for i, steps in enumerate((12, 7, 9)):
+        srv.submit(SV.Request(_scene(f"s{i}", 1000), steps))
+    peak = 0
+    while srv.poll():
+        peak = max(peak, len(srv.inflight))
+    assert peak <= 3
+    assert all(p.harvested for p in eng.pending)
+    assert len(srv.latencies_ms) == 12 + 7 + 9
+    assert eng.waits < len(eng.pending)  # most steps were harvested after they finished, not waited for
+    st = srv.stats()
+    assert st["request_latency_p50_s"] is not None and st["request_latency_p50_s"] <= st["request_latency_p99_s"]
+    assert st["resident_wall_ms_per_step_p50"] > 0
+    assert abs(st["aggregate_particle_steps_per_s"] - 1000 * 28 / (srv.busy_ms / 1e3)) < 1e-6

@@ -48,7 +48,11 @@ ALGO_BYTES = {"p2g": 64.0, "g2p": 147.0, "grid_update": 7.0}
 # 36-byte stress term to P2G's reads and G2P's writes
 STEP_BYTES = {"apic_mls": sum(ALGO_BYTES.values()), "pic": sum(ALGO_BYTES.values()),
               "apic_grad": sum(ALGO_BYTES.values()) + 72.0}
-KERNEL_SLOT = {"bin": 0, "scatter": 1, "p2g": 2, "grid_update": 3, "g2p": 4, "grid_list": 5, "g2p_fp64": 6}
+KERNEL_SLOT = {"bin": 0, "scatter": 1, "p2g": 2, "grid_update": 3, "g2p": 4, "grid_list": 5, "g2p_fp64": 6,
+               "g2p2g": 7}
+# The method's floor for one step: particle state x, v, B, F read and written
+# once (192 B) plus the dual grid (14 B per particle at 8 per cell)
+METHOD_FLOOR_BYTES = 206.0
 
 
 def _env_rank():
@@ -278,26 +282,150 @@ def _time_steps(ck, ctx, steps, stream_ptr):
     return a.elapsed_time(b)
 
 
-def served_mix(ck, stream_ptr, n_scenes=12, steps=40, scale=0.25, seed=0, budget_bytes=1 << 30):
-    """Continuous batching of a Poisson stream of scenes through the serving
-    loop: admission by a device-memory budget, one launch per kernel per
-    global step over every resident scene, retirement with readback."""
+def served_mix(ck, stream_ptr, n_scenes=64, steps=1000, n_max=2e6, seed=0, budget_bytes=24 << 30,
+               max_scenes=16, compress=20.0):
+    """Continuous batching of a Poisson stream of scenes (served-mix
+    configuration: 64 scenes, N log-uniform in [1e4, 2e6], 1000 steps each)
+    through the serving loop: admission by a device-memory budget, one launch
+    per kernel per global step over every resident scene, steps enqueued
+    without waiting, retirement with readback."""
     from paper_2412_10399_gb300 import scenes as S
     from paper_2412_10399_gb300 import serving as SV
-    reqs = S.served_mix(n_scenes=n_scenes, seed=seed, n_max=2e6 * scale, steps=steps)
-    budget = SV.Budget.from_bytes(budget_bytes, max_res=128, max_scenes=6)
+    reqs = S.served_mix(n_scenes=n_scenes, seed=seed, n_max=n_max, steps=steps)
+    budget = SV.Budget.from_bytes(budget_bytes, max_res=128, max_scenes=max_scenes)
     eng = SV.EngineCK(budget, stream=stream_ptr)
     srv = SV.Server(eng, budget)
     for r in reqs:
-        srv.submit(SV.Request(r.scene, r.scene.steps, arrival_s=r.arrival_s * 0.05, read_fields=(ck.FIELD_X,)))
+        srv.submit(SV.Request(r.scene, r.scene.steps, arrival_s=r.arrival_s / compress, read_fields=(ck.FIELD_X,)))
     srv.run()
     st = srv.stats()
     eng.close()
     st.update({"scenes": n_scenes, "steps_per_scene": steps, "budget_bytes": budget_bytes,
-               "mix": f"{n_scenes} scenes, N log-uniform in [1e4, {2e6 * scale:.0f}], box/sphere, elastic or "
-                      f"sand, {steps} steps each, Poisson arrivals (20 ms mean, time-compressed x20), "
-                      f"admitted under a {budget_bytes >> 20} MiB device budget"})
+               "particles_total": int(sum(r.scene.n for r in reqs)),
+               "mix": f"{n_scenes} scenes, N log-uniform in [1e4, {n_max:.0f}], box/sphere, elastic or sand, "
+                      f"{steps} steps each, Poisson arrivals (20 ms mean, time-compressed x{compress:g}), admitted "
+                      f"under a {budget_bytes >> 30} GiB device budget (at most {max_scenes} resident)",
+               "latency": "p50_ms/p99_ms: device time of the global step a scene step belonged to; "
+                          "request_latency_*: arrival to result (queue + admission + steps + readback); "
+                          "resident_wall_ms_per_step_*: a request's wall time per step while resident"})
     return st
+
+
+def impact_window(ck, scene, stream_ptr, start=75, steps=20):
+    """Steps start..start+steps of the large-impact scene, after the balls
+    reach the keep (about step 73): CK ms per step with no per-kernel events,
+    then the same window again with events around each launch; the largest
+    float64-pass count of a step in the window."""
+    ctx, keep = _make_ctx(ck, scene, ck.KERNEL_CK, stream_ptr)
+    ck.ckmpm_step(ctx, start)
+    ck.ckmpm_sync(ctx)
+    ms = _time_steps(ck, ctx, steps, stream_ptr)
+    ck.ckmpm_sync(ctx)
+    ck.ckmpm_destroy(ctx)
+    per_kernel, fp64_max = _kernel_breakdown(ck, scene, ck.KERNEL_CK, stream_ptr, start, steps)
+    return {"steps": f"{start}..{start + steps}", "ms_per_step": ms / steps, "value": scene.n * steps / (ms / 1e3),
+            "per_kernel_ms": per_kernel, "fp64_particles_max_step": fp64_max}
+
+
+def granular_column_lines(ck, stream_ptr, peak=None, steps=500):
+    """Granular column collapse (346,112 Drucker-Prager particles, 128^3,
+    dt 5e-5): all of its 500 steps, CK and the quadratic twin on identical
+    inputs, split and fused steps, device-resident."""
+    from paper_2412_10399_gb300 import scenes as S
+    sc = S.granular_column()
+    out = {}
+    for name, kernel in (("ck", ck.KERNEL_CK), ("quadratic", ck.KERNEL_QUADRATIC),
+                         ("ck_fused", ck.KERNEL_CK | ck.STEP_G2P2G),
+                         ("quadratic_fused", ck.KERNEL_QUADRATIC | ck.STEP_G2P2G)):
+        warm, keep = _make_ctx(ck, sc, kernel, stream_ptr)  # loads the kernels: the timed run starts at step 0
+        ck.ckmpm_step(warm, 3)
+        ck.ckmpm_destroy(warm)
+        ctx, keep = _make_ctx(ck, sc, kernel, stream_ptr)
+        ms = _time_steps(ck, ctx, steps, stream_ptr)
+        ck.ckmpm_sync(ctx)
+        ck.ckmpm_destroy(ctx)
+        out[name] = {"ms_per_step": ms / steps, "value": sc.n * steps / (ms / 1e3)}
+    out["ck_speedup"] = out["quadratic"]["ms_per_step"] / out["ck"]["ms_per_step"]
+    if peak:
+        out["ck"]["step_frac"] = _step_frac(STEP_BYTES["apic_mls"], sc.n, out["ck"]["ms_per_step"], peak)
+    out["workload"] = (f"granular column: 128^3, column cells [51,77)x[4,68)x[51,77), {sc.n} particles at 8 per "
+                       f"cell, DP sand E 3.5e5 nu 0.3 phi 30 rho 1600, dt 5e-5; steps 0..{steps}")
+    return out
+
+
+def fused_lines(ck, scene, stream_ptr, warmup, steps, peak=None):
+    """The fused G2P2G step (CKMPM_STEP_G2P2G) on the headline scene and
+    window, CK and quadratic, device-resident, with per-kernel times from a
+    second run; with peak (GB/s), the CK step against the method floor."""
+    out = {}
+    for name, kernel in (("ck", ck.KERNEL_CK), ("quadratic", ck.KERNEL_QUADRATIC)):
+        ctx, keep = _make_ctx(ck, scene, kernel | ck.STEP_G2P2G, stream_ptr)
+        ck.ckmpm_step(ctx, warmup)
+        ck.ckmpm_sync(ctx)
+        ms = _time_steps(ck, ctx, steps, stream_ptr)
+        ck.ckmpm_sync(ctx)
+        lo = int(ck.ckmpm_get_stats(ctx).leftover_particles)
+        ck.ckmpm_destroy(ctx)
+        per_kernel, _ = _kernel_breakdown(ck, scene, kernel | ck.STEP_G2P2G, stream_ptr, warmup, steps)
+        out[name] = {"ms_per_step": ms / steps, "value": scene.n * steps / (ms / 1e3), "per_kernel_ms": per_kernel,
+                     "leftover_particles_last_step": lo}
+    if peak:
+        out["ck"]["method_floor_frac"] = _step_frac(METHOD_FLOOR_BYTES, scene.n, out["ck"]["ms_per_step"], peak)
+    out["workload"] = f"{WORKLOAD}, steps {warmup}..{warmup + steps}"
+    return out
+
+
+def diff_lines(stream_ptr, steps=64, k=8):
+    """Differentiable configuration (262,144 particles, 128^3, 64 steps,
+    checkpoints every 8): forward ms per step, adjoint ms per step, and a
+    whole rollout (forward, then backward with recomputation from the
+    checkpoints) through torch.autograd."""
+    import torch
+    from paper_2412_10399_gb300 import diff as D
+    from paper_2412_10399_gb300 import scenes as S
+    sc = S.differentiable_cube()
+    dev = torch.device("cuda")
+    sim = D.DiffSim(sc, stream=stream_ptr)
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    x0 = torch.from_numpy(sc.x32()).to(dev)
+    v0 = torch.from_numpy(sc.v32()).to(dev)
+    E = torch.full((sc.n,), float(sc.materials[0].E), dtype=torch.float32, device=dev)
+    B0, F0 = D.initial_state(x0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        s = (x0, v0, B0, F0)
+        s = sim.step(*s, E)  # loads the kernels
+        torch.cuda.synchronize()
+        states = [(x0, v0, B0, F0)]
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(steps):
+            states.append(sim.step(*states[-1], E))
+        b.record(stream)
+        torch.cuda.synchronize()
+        fwd = a.elapsed_time(b) / steps
+        gE = torch.zeros_like(E)
+        adj = tuple(torch.zeros_like(t) for t in states[-1])
+        adj = (torch.ones_like(adj[0]),) + adj[1:]
+        a.record(stream)
+        for j in reversed(range(steps)):
+            adj = sim.step_backward(*states[j], E, *adj, gE)
+        b.record(stream)
+        torch.cuda.synchronize()
+        bwd = a.elapsed_time(b) / steps
+        x0r, v0r, Er = x0.clone().requires_grad_(True), v0.clone().requires_grad_(True), E.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xT, vT = D.Rollout.apply(x0r, v0r, Er, sim, steps, k)
+        loss = D.com_loss(xT, xT.detach().mean(0) + 0.01)
+        loss.backward()
+        torch.cuda.synchronize()
+        roll = time.perf_counter() - t0
+    sim.close()
+    return {"forward_ms_per_step": fwd, "adjoint_ms_per_step": bwd, "adjoint_over_forward": bwd / fwd,
+            "rollout_forward_backward_s": roll, "particles": sc.n, "steps": steps, "checkpoint_every": k,
+            "workload": "differentiable cube: 128^3, cells [48,80)^3, 262,144 FC particles, dt 1e-4, v = (0.5,0,0) "
+                        "+ N(0, 0.5^2); the rollout's backward replays each 8-step segment from its checkpoint"}
 
 
 # The paper's G2P2G kernel times per substep for the dam-break scenes (its
@@ -418,7 +546,9 @@ def run_gpu(args):
                 "algorithmic_bytes_per_particle": ALGO_BYTES[dominant], "traffic": traffic,
                 "per_kernel_ms": per_kernel,
                 "step_algorithmic_bytes_per_particle": sum(ALGO_BYTES.values()),
-                "step_frac": sum(ALGO_BYTES.values()) * n / (ms / args.steps / 1e3) / 1e9 / peak}
+                "step_frac": sum(ALGO_BYTES.values()) * n / (ms / args.steps / 1e3) / 1e9 / peak,
+                "method_floor_bytes_per_particle": METHOD_FLOOR_BYTES,
+                "step_frac_method_floor": METHOD_FLOOR_BYTES * n / (ms / args.steps / 1e3) / 1e9 / peak}
 
     # ---------------- quadratic B-spline twin on the same inputs and steps
     qsteps = args.steps
@@ -469,6 +599,11 @@ def run_gpu(args):
     dam = dam_break_lines(ck, stream_ptr, args.warmup, args.steps, peak=peak) if not args.no_dam else None
     transfers = (transfer_lines(ck, scene, stream_ptr, args.warmup, args.steps, peak=peak)
                  if not args.no_transfers else None)
+    extra = not args.no_extra and not args.max_particles
+    impact = impact_window(ck, scene, stream_ptr) if extra else None
+    column = granular_column_lines(ck, stream_ptr, peak=peak) if extra else None
+    fused = fused_lines(ck, scene, stream_ptr, args.warmup, args.steps, peak=peak) if not args.no_extra else None
+    diffl = diff_lines(stream_ptr) if extra else None
     cb = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu) else None
 
     if rank == 0:
@@ -483,7 +618,8 @@ def run_gpu(args):
                                     f"the keep from about step 73)",
                            "per_kernel_ms": "second run over the same steps with CUDA events around each launch"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "quadratic": quad, "served": served, "dam_break": dam, "transfers": transfers}
+                "clocks": clocks, "quadratic": quad, "served": served, "dam_break": dam, "transfers": transfers,
+                "impact": impact, "granular_column": column, "fused": fused, "diff": diffl}
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -504,6 +640,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-dam", action="store_true", help="skip the dam-break lines")
     ap.add_argument("--no-transfers", action="store_true", help="skip the kernel-gradient transfer lines")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the impact window, granular column, fused-step and differentiation lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -112,6 +112,7 @@ struct StepView {
   uint32_t n_keys;      // size of the key space
   uint32_t n_cur;       // particles in cur (including dead ones)
   uint32_t keep_gacc;   // probe: the grid update leaves Gacc, P2G keeps bnd_cur
+  uint32_t splits;      // work units per particle block of the transfer kernels (>= 1)
   // fused G2P2G step only (else null): the block table of the next step's
   // grid (the gather reads Gvel through `table`, the scatter adds to Gacc
   // through these), and the list of particles the fused kernel leaves to the
@@ -125,6 +126,22 @@ struct StepView {
 };
 
 __device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }
+
+// Work unit u of the transfer kernels: particle block u / splits, part
+// u % splits of its particles, in whole chunks of `align` particles (a step
+// with few blocks splits each over several units so that every resident
+// warp gets work).  Returns false when that part is empty.
+__device__ __forceinline__ bool unit_range(const StepView& v, uint32_t u, uint32_t align, uint32_t& bi,
+                                           uint32_t& lo, uint32_t& hi) {
+  const uint32_t S = v.splits;
+  bi = u / S;
+  const uint32_t part = u - bi * S;
+  const uint32_t cnt = v.cnt_cur[v.pb_key[bi]];
+  const uint32_t per = ((cnt + S - 1) / S + align - 1) / align * align;
+  lo = part * per;
+  hi = min(cnt, lo + per);
+  return lo < hi;
+}
 
 // Cell decomposition shared by every kernel that maps a position to nodes.
 // u0 = x/dx.  CK: t = u0 + 1/4, b+ = floor(t), f+ = t - b+ (exact when dx is a

@@ -107,6 +107,7 @@ struct ckmpm_ctx {
   // fused G2P2G steps: a second block-table set for the next step's grid,
   // which one maps the current grid velocities, and whether they are current
   bool fused = false;
+  int splits_override = 0;  // CKMPM_SPLITS: work units per block (else chosen from the particle count)
   int tsel = 0;
   bool grid_valid = false;
   uint32_t *table1 = nullptr, *g_list1 = nullptr, *g_scene1 = nullptr, *lo_list = nullptr;
@@ -243,6 +244,16 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.n_keys = (uint32_t)std::max<int64_t>(ctx->keys_alloc.high, 1);
   v.n_cur = (uint32_t)ctx->n_cur;
   v.keep_gacc = 0;
+  // a step with few particles splits each block over several work units, so
+  // that the resident warps of the transfer kernels (about 20 per SM) get two
+  // units of a few hundred particles each; large steps keep whole blocks
+  {
+    int64_t n_live = 0;
+    for (auto& s : ctx->scenes) n_live += s.alive ? s.n : 0;
+    const int64_t target = (int64_t)ctx->sm_count * 20 * 2 * 512;
+    v.splits = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(8, target / std::max<int64_t>(n_live, 1)));
+    if (ctx->splits_override > 0) v.splits = (uint32_t)ctx->splits_override;
+  }
   if (ctx->fused) {  // binning zeroes the leftover count every step
     v.lo_list = ctx->lo_list;
     v.lo_count = ctx->counters + 9;
@@ -459,6 +470,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   // quadratic twin (27-node stencils collide more), one for the compact kernel
   ctx->lc.p2g_rep = ctx->kind == 1 ? 2 : 1;
   if (const char* e = getenv("CKMPM_P2G_REP")) ctx->lc.p2g_rep = atoi(e) == 2 ? 2 : 1;
+  if (const char* e = getenv("CKMPM_SPLITS")) ctx->splits_override = std::max(1, std::min(8, atoi(e)));
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {

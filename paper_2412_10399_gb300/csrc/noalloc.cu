@@ -186,6 +186,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   v.n_keys = (uint32_t)nkeys;
   v.n_cur = (uint32_t)n;
   v.keep_gacc = 1;
+  v.splits = 1;
   bs.scene_tab = scene_tab;
   bs.n_scene_tab = 1;
 

@@ -702,14 +702,16 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
   __shared__ float4 sT0[TCAP], sT1[TCAP];
   __shared__ float sT2[TCAP];
   __shared__ uint32_t bslot[8];
-  const uint32_t npb = *v.n_pb;
+  const uint32_t nunits = *v.n_pb * v.splits;
   const uint32_t lane = threadIdx.x;
   for (;;) {
-    // dynamic scheduling: one block at a time from a counter
-    uint32_t bi = 0;
-    if (lane == 0) bi = atomicAdd(&v.work[0], 1u);
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (bi >= npb) break;
+    // dynamic scheduling: one work unit (a block or a part of one) at a time
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(&v.work[0], 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) break;
+    uint32_t bi, lo, hi;
+    if (!unit_range(v, u, CAP, bi, lo, hi)) continue;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
@@ -722,11 +724,12 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
     for (int j = lane; j < REP * RS / 4; j += kP2GWarp) reinterpret_cast<int4*>(small)[j] = make_int4(0, 0, 0, 0);
+    // the scale covers the block's whole count, so any part of it is bounded
     const float fcnt = (float)cnt;
     const float Sm = bmass > 0.f ? 1073741824.0f / (fcnt * bmass) : 1.0f;
     const float Sp = bmom > 0.f ? 1073741824.0f / (fcnt * bmom) : 1.0f;
-    for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
-      const uint32_t m = min(cnt - c0, CAP);
+    for (uint32_t c0 = lo; c0 < hi; c0 += CAP) {
+      const uint32_t m = min(hi - c0, CAP);
 #pragma unroll
       for (uint32_t r = 0; r < C; ++r) {
         const uint32_t i = lane + r * kP2GWarp;
@@ -782,13 +785,9 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
                                              (float)q[3] * iSp));
       }
     }
-    // the bounds are used: clear them for the step that next bins into this
-    // buffer (a probe reruns this P2G on the same particles and keeps them)
-    if (lane == 0 && !v.keep_gacc) {
-      v.bnd_cur[2 * key] = 0u;
-      v.bnd_cur[2 * key + 1] = 0u;
-    }
-    __syncwarp();  // the next block clears the accumulators
+    // (the block's bounds are cleared after G2P, by the float64 pass: other
+    // units of this block may still be reading them)
+    __syncwarp();  // the next unit clears the accumulators
   }
 }
 
@@ -1030,24 +1029,26 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
   __shared__ float sF2[CAP], sE[CAP];
   __shared__ uint32_t sID[CAP];
   __shared__ uint32_t bslot[8];
-  const uint32_t npb = *v.n_pb;
+  const uint32_t nunits = *v.n_pb * v.splits;
   for (;;) {
-    // blocks are handed out one at a time (dynamic scheduling: block costs
-    // vary with their particle counts and constitutive work)
-    uint32_t bi = 0;
-    if (threadIdx.x == 0) bi = atomicAdd(&v.work[1], 1u);
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (bi >= npb) break;
+    // work units (a block or a part of one) are handed out one at a time
+    // (dynamic scheduling: their costs vary with particle counts and
+    // constitutive work)
+    uint32_t u = 0;
+    if (threadIdx.x == 0) u = atomicAdd(&v.work[1], 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) break;
+    uint32_t bi, lo, hi;
+    if (!unit_range(v, u, CAP, bi, lo, hi)) continue;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
-    const uint32_t cnt = v.cnt_cur[key];
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
     __syncwarp();
-    for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
-    const uint32_t m = min(cnt - c0, (uint32_t)CAP);
+    for (uint32_t c0 = lo; c0 < hi; c0 += CAP) {
+    const uint32_t m = min(hi - c0, (uint32_t)CAP);
     // the chunk's particle state and (first chunk) the block's grid
     // velocities: cp.async gathers, all in flight before the one wait
 #pragma unroll 4
@@ -1060,7 +1061,7 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
       cp_async4(&sID[i], &v.cur.ID[p]);
       if (v.cur.E) cp_async4(&sE[i], &v.cur.E[p]);
     }
-    if (c0 == 0) {
+    if (c0 == lo) {
       for (int j = threadIdx.x; j < NS; j += blockDim.x) {
         int g, lx, ly, lz;
         staged_coords<KIND>(j, g, lx, ly, lz);
@@ -1079,11 +1080,8 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
                                  v.cur.E ? sE[i] : 0.f, o))
         warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, o.nk, o.bmass, o.bmom);
     }
-    __syncwarp();  // the next chunk (or block) overwrites the staged copies
+    __syncwarp();  // the next chunk (or unit) overwrites the staged copies
     }
-    // last use of the block's count this step: clear it, so that this buffer
-    // is all zero when G2P fills it as the next histogram
-    if (threadIdx.x == 0) v.cnt_cur[key] = 0u;
   }
 }
 
@@ -1149,18 +1147,19 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
   __shared__ uint32_t bslot[8];
   auto& p1 = *reinterpret_cast<typename SM::Ph1*>(arena);
   auto& p2 = *reinterpret_cast<typename SM::Ph2*>(arena);
-  const uint32_t npb = *v.n_pb;
+  const uint32_t nunits = *v.n_pb * v.splits;
   const uint32_t lane = threadIdx.x;
   for (;;) {
-    uint32_t bi = 0;
-    if (lane == 0) bi = atomicAdd(&v.work[1], 1u);
-    bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (bi >= npb) break;
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(&v.work[1], 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) break;
+    uint32_t bi, lo, hi;
+    if (!unit_range(v, u, CAP, bi, lo, hi)) continue;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
-    const uint32_t cnt = v.cnt_cur[key];
-    const bool track = cnt <= (uint32_t)kFuseMaxCnt;
+    const bool track = hi - lo <= (uint32_t)kFuseMaxCnt;
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);  // this step's grid (gather)
@@ -1168,8 +1167,8 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
     // ---- pass 1: G2P of the block
     float bm_max = 0.f, bp_max = 0.f;
     uint32_t nstay = 0;
-    for (uint32_t c0 = 0; c0 < cnt; c0 += CAP) {
-      const uint32_t m = min(cnt - c0, (uint32_t)CAP);
+    for (uint32_t c0 = lo; c0 < hi; c0 += CAP) {
+      const uint32_t m = min(hi - c0, (uint32_t)CAP);
 #pragma unroll 4
       for (uint32_t i = lane; i < m; i += 32) {
         const uint32_t p = v.perm[start + c0 + i];
@@ -1180,7 +1179,7 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
         cp_async4(&p1.sID[i], &v.cur.ID[p]);
         if (v.cur.E) cp_async4(&p1.sE[i], &v.cur.E[p]);
       }
-      if (c0 == 0) {
+      if (c0 == lo) {
         for (int j = lane; j < NS; j += 32) {
           int g, lx, ly, lz;
           staged_coords<KIND>(j, g, lx, ly, lz);
@@ -1208,7 +1207,7 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
         warp_append(v.lo_count, v.lo_list, t, ok && !st);
         const unsigned am = __activemask();
         const unsigned w = __ballot_sync(am, st);
-        if (track && (int)lane == __ffs(am) - 1) stay[(c0 + i - lane) >> 5] = w;
+        if (track && (int)lane == __ffs(am) - 1) stay[(c0 - lo + i - lane) >> 5] = w;
       }
       __syncwarp();  // the next chunk overwrites the staged copies
     }
@@ -1225,8 +1224,8 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
       const float fst = (float)nstay;
       const float Sm = bm_max > 0.f ? 1073741824.0f / (fst * bm_max) : 1.0f;
       const float Sp = bp_max > 0.f ? 1073741824.0f / (fst * bp_max) : 1.0f;
-      for (uint32_t c0 = 0; c0 < cnt; c0 += PCAP) {
-        const uint32_t m = min(cnt - c0, PCAP);
+      for (uint32_t c0 = lo; c0 < hi; c0 += PCAP) {
+        const uint32_t m = min(hi - c0, PCAP);
 #pragma unroll
         for (uint32_t r = 0; r < PC; ++r) {
           const uint32_t i = lane + r * 32;
@@ -1243,7 +1242,7 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
 #pragma unroll 1
         for (uint32_t r = 0; r < PC; ++r) {
           const uint32_t i = lane * PC + r;
-          const uint32_t q = c0 + i;
+          const uint32_t q = c0 - lo + i;
           if (i < m && ((stay[q >> 5] >> (q & 31)) & 1u)) {
             const P2GPart part{p2.sX[i], p2.sA[i], p2.sB[i], p2.sC[i]};
             p2g_scatter<KIND>(s, v.mats, v.err, part, ox, oy, oz, Sm, Sp, p2.sm);
@@ -1266,13 +1265,7 @@ __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p2g(StepView v) {
         }
       }
     }
-    // last use of the block's count and bounds this step
-    if (lane == 0) {
-      v.cnt_cur[key] = 0u;
-      v.bnd_cur[2 * key] = 0u;
-      v.bnd_cur[2 * key + 1] = 0u;
-    }
-    __syncwarp();  // the next block reuses the arena and the slots
+    __syncwarp();  // the next unit reuses the arena and the slots
   }
 }
 
@@ -1350,6 +1343,16 @@ __global__ void __launch_bounds__(128) k_p2g_leftover(StepView v) {
 // Grid-stride over the list; an empty list returns at once.
 template <int KIND>
 __global__ void __launch_bounds__(128) k_g2p_fp64(StepView v) {
+  // every transfer kernel of the step is done with the histogram entries and
+  // P2G bounds of this step's blocks: clear them, so that this buffer is all
+  // zero when G2P fills it for the step after next
+  const uint32_t npb = *v.n_pb;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npb; i += gridDim.x * blockDim.x) {
+    const uint32_t key = v.pb_key[i];
+    v.cnt_cur[key] = 0u;
+    v.bnd_cur[2 * key] = 0u;
+    v.bnd_cur[2 * key + 1] = 0u;
+  }
   const uint32_t n = (uint32_t)min(*v.fp64_count, (unsigned long long)v.n_cur);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t t = v.fp64_list[i];

@@ -262,3 +262,38 @@ def test_apic_grad_B_roundtrip_and_static_entry_refuses():
         ck.ckmpm_p2g_grids_static(scs, ck.kernel_code(sc), 0, 0, gm.data_ptr(), gp.data_ptr(),
                                   torch.cuda.current_stream().cuda_stream)
     assert e.value.status == ck.EINVAL
+
+
+@pytest.mark.parametrize("transfer", [S.TRANSFER_PIC, S.TRANSFER_APIC_GRAD])
+@pytest.mark.parametrize("model", MODELS)
+def test_kernel_gradient_transfers_float64_pass_two_steps(transfer, model):
+    """Every other particle has a nearly singular F (J ~ 1e-3), so the default
+    criteria send it to the float64 pass, which under PIC stores -dt V0 tau in
+    the state's M slot and under the kernel-gradient APIC in the separate
+    stress arrays; the next step's P2G reads them.  Two steps against the
+    oracle, with the float32 bounds of the two-step float64-pass test of the
+    APIC + MLS transfer (F within 5e-6, v within 2e-4 relative)."""
+    ck = need_gpu()
+    sc, B, F = random_scene(3000, 16, 47, model=model, f_scale=0.02)
+    sc.transfer = transfer
+    F = F.astype(np.float64)
+    F[::2, :, 2] *= 1e-3
+    F = f32(F)
+    sim = ck.Simulation(sc, ck.kernel_code(sc))
+    sim.write(ck.FIELD_F, F)
+    if transfer == S.TRANSFER_APIC_GRAD:
+        sim.write(ck.FIELD_B, B)
+    else:
+        B = np.zeros_like(B)
+    sim.step(1)
+    sim.sync()
+    n64 = int(sim.stats().fp64_particles)
+    sim.step(1)
+    sim.sync()
+    Fg = sim.read(ck.FIELD_F)
+    vg = sim.read(ck.FIELD_V)
+    sim.close()
+    assert n64 >= sc.n // 2 - 5
+    st2 = O.run(oracle_state(sc, B, F), O.params_from_scene(sc), 2)
+    assert rel(Fg, st2.F.numpy()) <= 5e-6
+    assert rel(vg, st2.v.numpy()) <= 2e-4

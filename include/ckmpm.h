@@ -189,6 +189,7 @@ typedef struct {
   int64_t launches_kernel[8]; /* launches counted in ms_kernel */
   int64_t launches_per_step;  /* kernel launches issued by one step */
   int64_t leftover_particles; /* fused steps: particles of the last step's leftover P2G */
+  int64_t graph_steps;        /* steps launched as a CUDA graph (see ckmpm_step) */
 } ckmpm_stats;
 
 /* Create a context holding one scene (scene id 0) with capacities equal to
@@ -212,7 +213,14 @@ CKMPM_API ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id);
 /* Enqueue n time steps of every resident scene on the context's stream.
  * Asynchronous: device-side errors (EDOMAIN, ENONFINITE) surface at the next
  * ckmpm_sync / ckmpm_readback.  Returns EINVAL for n < 0, ECUDA on a launch
- * failure, or the sticky error of an earlier step. */
+ * failure, or the sticky error of an earlier step.
+ * A steady step (no admission, release, upload or probe since the previous
+ * one, timing off) is captured once into a CUDA graph per parity of the
+ * double-buffered state and replayed after that, which saves the launch
+ * gaps of its nine to eleven kernels; any of those operations drops the
+ * graphs.  A stream that cannot be captured (the legacy default stream, or
+ * one the caller is capturing) gets direct launches.  CKMPM_GRAPHS=0 in the
+ * environment turns graphs off for contexts created afterwards. */
 CKMPM_API ckmpm_status ckmpm_step(ckmpm_ctx* ctx, int n);
 
 /* Wait for the context's stream and return the first device error (sticky). */

@@ -63,7 +63,8 @@ class ckmpm_stats(ctypes.Structure):
                 ("n_grid_blocks", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("fp64_particles", ctypes.c_int64), ("ms_last_step", ctypes.c_double),
                 ("ms_kernel", ctypes.c_double * 8), ("launches_kernel", ctypes.c_int64 * 8),
-                ("launches_per_step", ctypes.c_int64), ("leftover_particles", ctypes.c_int64)]
+                ("launches_per_step", ctypes.c_int64), ("leftover_particles", ctypes.c_int64),
+                ("graph_steps", ctypes.c_int64)]
 
 
 # Every symbol the header declares, with its signature.

@@ -108,6 +108,12 @@ struct ckmpm_ctx {
   // which one maps the current grid velocities, and whether they are current
   bool fused = false;
   int splits_override = 0;  // CKMPM_SPLITS: work units per block (else chosen from the particle count)
+  // steady-state steps replayed as CUDA graphs, one per parity of the
+  // double-buffered state (particle buffer cur, plus table set tsel for
+  // fused steps); dropped whenever the launch sequence or its arguments change
+  bool graphs = false;
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t graph_steps = 0;  // steps launched as a graph
   int tsel = 0;
   bool grid_valid = false;
   uint32_t *table1 = nullptr, *g_list1 = nullptr, *g_scene1 = nullptr, *lo_list = nullptr;
@@ -471,6 +477,10 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   ctx->lc.p2g_rep = ctx->kind == 1 ? 2 : 1;
   if (const char* e = getenv("CKMPM_P2G_REP")) ctx->lc.p2g_rep = atoi(e) == 2 ? 2 : 1;
   if (const char* e = getenv("CKMPM_SPLITS")) ctx->splits_override = std::max(1, std::min(8, atoi(e)));
+  // steady steps run as CUDA graphs (CKMPM_GRAPHS=0 turns them off); the
+  // legacy stream cannot be captured, so a context on it launches directly
+  ctx->graphs = true;
+  if (const char* e = getenv("CKMPM_GRAPHS")) ctx->graphs = atoi(e) != 0;
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {
@@ -478,6 +488,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
     ctx->own_stream = true;
   }
   ctx->lc.stream = ctx->stream;
+  if (!ctx->stream) ctx->graphs = false;
   ctx->cap_n = cfg->max_particles;
   ctx->cap_keys = cfg->max_keys;
   ctx->cap_pool = cfg->max_grid_blocks;
@@ -539,6 +550,51 @@ bool capturing(ckmpm_ctx* ctx) {
   return st != cudaStreamCaptureStatusNone;
 }
 
+void drop_graphs(ckmpm_ctx* ctx) {
+  for (auto& g : ctx->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Run a step's launch sequence as the CUDA graph of state parity `key`,
+// capturing it on first use; false when the step must be issued directly
+// instead (capture is not possible on this stream -- the legacy stream, or
+// one the caller is capturing itself -- or it failed; graphs are then off
+// for the context and nothing of the sequence has run).
+template <typename Issue>
+bool graph_step(ckmpm_ctx* ctx, int key, Issue&& issue) {
+  if (!ctx->graphs) return false;
+  cudaGraphExec_t& ex = ctx->gexec[key];
+  if (!ex) {
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->graphs = false;
+      return false;
+    }
+    issue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      ex = nullptr;
+      ctx->graphs = false;
+      return false;
+    }
+    cudaGraphDestroy(g);
+  }
+  if (cudaGraphLaunch(ex, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    drop_graphs(ctx);
+    ctx->graphs = false;
+    return false;
+  }
+  ctx->graph_steps++;
+  return true;
+}
+
 ckmpm_status run_step_fused(ckmpm_ctx* ctx);
 
 ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
@@ -546,6 +602,8 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   if (ctx->fused) ctx->grid_valid = false;  // a probe reuses the grid arrays
   ck::StepView v = make_view(ctx);
   ckmpm_ctx::EvPair ep{};
+  const bool steady = !probe && !ctx->timing && !ctx->grids_dirty && !ctx->keys_dirty;
+  if (probe) drop_graphs(ctx);  // the probe refills the block table the graphs were captured with
   if (ctx->grids_dirty) {
     ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_CLEAR);
     ctx->grids_dirty = false;
@@ -578,6 +636,8 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   // set is cleared before it is filled again (a probe fills set tsel)
   if (ctx->fused) ck::launch_table_reset(ctx->stream, v.table, v.g_list, v.n_g, v.pool_cap, grid_ctas);
   if (ctx->timing && !probe) cudaEventRecord(ctx->step_a, ctx->stream);
+  v.keep_gacc = probe ? 1u : 0u;
+  auto issue = [&]() {
   tbeg(ctx, ep, 0);
   ck::launch_bin(ctx->stream, v, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
   ck::launch_bin(ctx->stream, v, bs, ck::LB_SCAN_TOP, ngb, grid_ctas);
@@ -589,27 +649,32 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
   tbeg(ctx, ep, 5);
   ck::launch_bin(ctx->stream, v, bs, ck::LB_GLIST, ngb, grid_ctas);
   tend(ctx, ep);
-  v.keep_gacc = probe ? 1u : 0u;
   tbeg(ctx, ep, 2);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_P2G);
   tend(ctx, ep);
   tbeg(ctx, ep, 3);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_UPDATE);
   tend(ctx, ep);
-  if (probe) {
-    ctx->grids_dirty = true;
-    CK_TRY(cudaGetLastError(), "probe launch");
-    return CKMPM_OK;
-  }
+  if (probe) return;
   tbeg(ctx, ep, 4);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_G2P);
   tend(ctx, ep);
   tbeg(ctx, ep, 6);
   ck::launch_transfer(ctx->kind, ctx->lc, v, ck::LK_G2P_FP64);
   tend(ctx, ep);
+  };
+  if (!(steady && !ctx->fused && graph_step(ctx, ctx->cur, issue))) issue();
+  if (probe) {
+    ctx->grids_dirty = true;
+    CK_TRY(cudaGetLastError(), "probe launch");
+    return CKMPM_OK;
+  }
   if (ctx->timing) cudaEventRecord(ctx->step_b, ctx->stream);
   CK_TRY(cudaGetLastError(), "step launch");
   ctx->cur ^= 1;
+  // a step that drops released particles changes the pool's count, which the
+  // graphs were captured with
+  if (ctx->n_cur != n_live) drop_graphs(ctx);
   ctx->n_cur = n_live;
   rebuild_layout_sorted(ctx);
   ctx->steps++;
@@ -627,6 +692,7 @@ ckmpm_status run_step(ckmpm_ctx* ctx, bool probe) {
 // float64 pass; the leftover P2G (claiming any further grid blocks); the grid
 // update of the new grid; and the sets swap.
 ckmpm_status run_step_fused(ckmpm_ctx* ctx) {
+  const bool was_clean = !ctx->grids_dirty && !ctx->keys_dirty && ctx->grid_valid && !ctx->timing;
   if (ctx->grids_dirty) {
     ck::launch_transfer(ctx->kind, ctx->lc, make_view(ctx), ck::LK_CLEAR);
     ctx->grids_dirty = false;
@@ -664,11 +730,51 @@ ckmpm_status run_step_fused(ckmpm_ctx* ctx) {
   ctx->tsel = cs;
   ckmpm_ctx::EvPair ep{};
   if (ctx->timing) cudaEventRecord(ctx->step_a, ctx->stream);
-  // every table set is cleared of the entries its last fill assigned (its
-  // list records them, slots claimed by the leftover P2G included) before it
-  // is filled again
-  ck::launch_table_reset(ctx->stream, vn.table, vn.g_list, vn.n_g, vn.pool_cap, grid_ctas);
-  if (!ctx->grid_valid) {
+  // the fused kernel gathers through set cs and scatters through set ns
+  ck::StepView vf = vc;
+  vf.table_nxt = vn.table;
+  vf.g_list_nxt = vn.g_list;
+  vf.g_scene_nxt = vn.g_scene;
+  vf.n_g_nxt = vn.n_g;
+  auto issue_fused = [&]() {
+    tbeg(ctx, ep, 7);
+    ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_G2P2G);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 6);
+    ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_G2P_FP64);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 2);
+    ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_LEFTOVER);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 3);
+    ck::launch_transfer(ctx->kind, ctx->lc, vn, ck::LK_UPDATE);
+    tend(ctx, ep);
+  };
+  // the steady step: the next table set cleared and filled from this step's
+  // blocks, then the fused kernel, the float64 pass, the leftover P2G and the
+  // grid update
+  auto issue_steady = [&]() {
+    ck::launch_table_reset(ctx->stream, vn.table, vn.g_list, vn.n_g, vn.pool_cap, grid_ctas);
+    tbeg(ctx, ep, 0);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_TOP, ngb, grid_ctas);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 1);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCATTER, ngb, grid_ctas);
+    tend(ctx, ep);
+    tbeg(ctx, ep, 5);
+    ck::launch_bin(ctx->stream, vn, bs, ck::LB_GLIST, ngb, grid_ctas);
+    tend(ctx, ep);
+    issue_fused();
+  };
+  if (ctx->grid_valid) {
+    if (!(was_clean && graph_step(ctx, ctx->cur + 2 * ctx->tsel, issue_steady))) issue_steady();
+  } else {
+    // every table set is cleared of the entries its last fill assigned (its
+    // list records them, slots claimed by the leftover P2G included) before
+    // it is filled again
+    ck::launch_table_reset(ctx->stream, vn.table, vn.g_list, vn.n_g, vn.pool_cap, grid_ctas);
     // prologue: binning, P2G and grid update of the current state into set cs
     ck::launch_table_reset(ctx->stream, vc.table, vc.g_list, vc.n_g, vc.pool_cap, grid_ctas);
     ck::launch_bin(ctx->stream, vc, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
@@ -682,42 +788,14 @@ ckmpm_status run_step_fused(ckmpm_ctx* ctx) {
     CK_TRY(cudaMemsetAsync(vn.n_g, 0, sizeof(uint32_t), ctx->stream), "memset");
     ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
     ck::launch_bin(ctx->stream, vn, bs, ck::LB_GLIST, ngb, grid_ctas);
+    issue_fused();
     ctx->grid_valid = true;
-  } else {
-    tbeg(ctx, ep, 0);
-    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_TILES, ngb, grid_ctas);
-    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_TOP, ngb, grid_ctas);
-    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCAN_FINAL, ngb, grid_ctas);
-    tend(ctx, ep);
-    tbeg(ctx, ep, 1);
-    ck::launch_bin(ctx->stream, vn, bs, ck::LB_SCATTER, ngb, grid_ctas);
-    tend(ctx, ep);
-    tbeg(ctx, ep, 5);
-    ck::launch_bin(ctx->stream, vn, bs, ck::LB_GLIST, ngb, grid_ctas);
-    tend(ctx, ep);
   }
-  // the fused kernel gathers through set cs and scatters through set ns
-  ck::StepView vf = vc;
-  vf.table_nxt = vn.table;
-  vf.g_list_nxt = vn.g_list;
-  vf.g_scene_nxt = vn.g_scene;
-  vf.n_g_nxt = vn.n_g;
-  tbeg(ctx, ep, 7);
-  ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_G2P2G);
-  tend(ctx, ep);
-  tbeg(ctx, ep, 6);
-  ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_G2P_FP64);
-  tend(ctx, ep);
-  tbeg(ctx, ep, 2);
-  ck::launch_transfer(ctx->kind, ctx->lc, vf, ck::LK_LEFTOVER);
-  tend(ctx, ep);
-  tbeg(ctx, ep, 3);
-  ck::launch_transfer(ctx->kind, ctx->lc, vn, ck::LK_UPDATE);
-  tend(ctx, ep);
   if (ctx->timing) cudaEventRecord(ctx->step_b, ctx->stream);
   CK_TRY(cudaGetLastError(), "step launch");
   ctx->cur ^= 1;
   ctx->tsel = ns;
+  if (ctx->n_cur != n_live) drop_graphs(ctx);
   ctx->n_cur = n_live;
   rebuild_layout_sorted(ctx);
   ctx->steps++;
@@ -881,6 +959,7 @@ ckmpm_status admit_impl(ckmpm_ctx* ctx, const ckmpm_scene* sc, int* scene_id) {
   }
   ctx->layout.push_back({slot, ctx->n_cur, sc->n});
   ctx->grid_valid = false;
+  drop_graphs(ctx);  // particle count, key space and scene table changed
   ctx->n_cur += sc->n;
   if (scene_id) *scene_id = slot;
   return CKMPM_OK;
@@ -984,6 +1063,7 @@ ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id) {
          "memset");
   h.alive = false;
   ctx->grid_valid = false;
+  drop_graphs(ctx);
   ctx->h_scenes[scene_id].alive = 0;
   CK_TRY(cudaMemcpyAsync(ctx->d_scenes + scene_id, &ctx->h_scenes[scene_id], sizeof(SceneDev), cudaMemcpyHostToDevice,
                          ctx->stream),
@@ -1115,6 +1195,7 @@ ckmpm_status ckmpm_upload(ckmpm_ctx* ctx, int scene_id, int field, const void* s
   // keys (positions) or P2G bounds (velocity, M through B, F or E) changed:
   // the next step re-bins the pool first
   ctx->keys_dirty = true;
+  drop_graphs(ctx);
   return read_device_error(ctx);
 }
 
@@ -1128,6 +1209,7 @@ ckmpm_status ckmpm_get_stats(ckmpm_ctx* ctx, ckmpm_stats* out) {
   out->n_particle_blocks = c[0];
   out->n_grid_blocks = c[ctx->tsel == 0 ? 1 : 8];
   out->leftover_particles = ctx->fused ? c[9] : 0;
+  out->graph_steps = ctx->graph_steps;
   out->steps = ctx->steps;
   unsigned long long f64 = 0;
   std::memcpy(&f64, &c[4], sizeof(f64));
@@ -1167,6 +1249,7 @@ ckmpm_status ckmpm_reset_timing(ckmpm_ctx* ctx) {
 ckmpm_status ckmpm_destroy(ckmpm_ctx* ctx) {
   if (!ctx) return CKMPM_OK;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx);
   harvest_timing(ctx);
   for (auto& e : ctx->ev_free) {
     cudaEventDestroy(e.a);

@@ -271,8 +271,10 @@ def test_kernel_gradient_transfers_float64_pass_two_steps(transfer, model):
     criteria send it to the float64 pass, which under PIC stores -dt V0 tau in
     the state's M slot and under the kernel-gradient APIC in the separate
     stress arrays; the next step's P2G reads them.  Two steps against the
-    oracle, with the float32 bounds of the two-step float64-pass test of the
-    APIC + MLS transfer (F within 5e-6, v within 2e-4 relative)."""
+    oracle: v within 2e-4 relative (the two-step float64-pass test of the
+    APIC + MLS transfer), F within the 1e-5 this module states for the
+    kernel-gradient transfers (a node at the edge of a particle's support
+    carries its velocity error into grad v with the factor |grad w| / w)."""
     ck = need_gpu()
     sc, B, F = random_scene(3000, 16, 47, model=model, f_scale=0.02)
     sc.transfer = transfer
@@ -295,5 +297,5 @@ def test_kernel_gradient_transfers_float64_pass_two_steps(transfer, model):
     sim.close()
     assert n64 >= sc.n // 2 - 5
     st2 = O.run(oracle_state(sc, B, F), O.params_from_scene(sc), 2)
-    assert rel(Fg, st2.F.numpy()) <= 5e-6
+    assert rel(Fg, st2.F.numpy()) <= 1e-5
     assert rel(vg, st2.v.numpy()) <= 2e-4

@@ -25,8 +25,14 @@
  *    errors set a status word that ckmpm_sync() reports.
  *  - Pointers marked "host or device" are interpreted per the accompanying
  *    is_device flag; device pointers must be on the context's device.
- *  - Input arrays are borrowed for the duration of the call and copied; the
+ *  - Input arrays are borrowed and copied into the context's own state; the
  *    context owns all device state.  Output arrays are owned by the caller.
+ *    Calls that synchronise (ckmpm_upload, ckmpm_readback) are done with
+ *    their arrays on return.  ckmpm_create and ckmpm_admit read device
+ *    arrays and page-locked host arrays in stream order: those must stay
+ *    unchanged until the context's stream has passed the call (the next
+ *    ckmpm_sync or synchronising call); pageable host arrays are copied
+ *    before the call returns.
  *  - All floating-point state is float32; parameters are given in double and
  *    rounded once.
  */
@@ -203,7 +209,9 @@ CKMPM_API ckmpm_status ckmpm_create_server(const ckmpm_config* cfg, ckmpm_ctx** 
 
 /* Admit a scene into a context (continuous batching: takes effect at the next
  * step; resident scenes keep running).  ENOMEM if any capacity would be
- * exceeded (nothing changes).  *scene_id receives the scene's id. */
+ * exceeded (nothing changes).  *scene_id receives the scene's id.
+ * Host x, v, mat are copied into a device staging buffer on the context's
+ * stream (page-locked ones asynchronously; see Conventions). */
 CKMPM_API ckmpm_status ckmpm_admit(ckmpm_ctx* ctx, const ckmpm_scene* scene, int* scene_id);
 
 /* Remove a scene; its particles leave the pool at the next step and its
@@ -232,9 +240,36 @@ CKMPM_API ckmpm_status ckmpm_probe_grids(ckmpm_ctx* ctx);
 
 /* Copy a field of one scene into dst (host or device), in the scene's
  * original particle order.  bytes must equal the field size exactly.
- * Synchronises the stream.  EINVAL on a size mismatch. */
+ * Synchronises the stream.  EINVAL on a size mismatch.  A host dst goes
+ * through ckmpm_readback_async + ckmpm_readback_wait (no allocation once the
+ * staging slots have grown to the field's size). */
 CKMPM_API ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, size_t bytes,
                             int dst_is_device);
+
+/* Asynchronous host readback of the same fields (a state query between steps,
+ * not part of the paper's method).  Enqueues, on the context's stream, the
+ * gather of the field as the steps enqueued so far leave it into one of two
+ * device staging slots owned by the context, and, on a second stream of the
+ * context, the copy of that slot into host_dst; returns at once with
+ * *ticket >= 0.  Steps enqueued afterwards run while the copy proceeds.
+ * host_dst (bytes, exactly the field size) belongs to the caller and must
+ * stay valid and unread until ckmpm_readback_wait(ctx, *ticket) returns;
+ * page-locked memory (cudaHostAlloc / torch pin_memory) is needed for the
+ * copy to overlap, pageable memory makes the call wait for the copy.
+ * Tickets alternate between the two slots: a third call reuses the first
+ * slot and makes the context's stream wait (on the device, not the host)
+ * until that slot's previous copy has finished.
+ * Errors: as ckmpm_readback (EINVAL, ENOTFOUND, EBUSY under capture), ENOMEM
+ * when a slot cannot grow, ECUDA; *ticket is -1 on error. */
+CKMPM_API ckmpm_status ckmpm_readback_async(ckmpm_ctx* ctx, int scene_id, int field, void* host_dst, size_t bytes,
+                                            int64_t* ticket);
+
+/* Wait (on the host) until the copy of a ticket has reached its host buffer,
+ * then return the sticky device error as it stood when the field was
+ * gathered (EDOMAIN, ENONFINITE, ...).  Waiting on an older ticket than the
+ * last two waits for the newest copy of its slot.  EINVAL for a ticket this
+ * context never issued. */
+CKMPM_API ckmpm_status ckmpm_readback_wait(ckmpm_ctx* ctx, int64_t ticket);
 
 /* Overwrite a particle field (X, V, B, F, E) of one scene from src (host or
  * device), in the scene's original particle order.  bytes must equal the

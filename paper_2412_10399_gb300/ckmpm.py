@@ -78,6 +78,9 @@ SIGNATURES = {
     "ckmpm_sync": (ctypes.c_int, [_P]),
     "ckmpm_probe_grids": (ctypes.c_int, [_P]),
     "ckmpm_readback": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
+    "ckmpm_readback_async": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_int64)]),
+    "ckmpm_readback_wait": (ctypes.c_int, [_P, ctypes.c_int64]),
     "ckmpm_upload": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
     "ckmpm_scene_particles": (ctypes.c_int64, [_P, ctypes.c_int]),
     "ckmpm_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ckmpm_stats)]),
@@ -169,6 +172,16 @@ def ckmpm_probe_grids(ctx):
 
 def ckmpm_readback(ctx, scene_id: int, field: int, dst_ptr: int, nbytes: int, dst_is_device: bool):
     _check(load().ckmpm_readback(ctx, scene_id, field, _P(dst_ptr), nbytes, int(dst_is_device)), ctx)
+
+
+def ckmpm_readback_async(ctx, scene_id: int, field: int, host_ptr: int, nbytes: int) -> int:
+    t = ctypes.c_int64(-1)
+    _check(load().ckmpm_readback_async(ctx, scene_id, field, _P(host_ptr), nbytes, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def ckmpm_readback_wait(ctx, ticket: int):
+    _check(load().ckmpm_readback_wait(ctx, ticket), ctx)
 
 
 def ckmpm_upload(ctx, scene_id: int, field: int, src_ptr: int, nbytes: int, src_is_device: bool):

@@ -125,6 +125,20 @@ struct ckmpm_ctx {
   MatDev* d_mats = nullptr;
   void* staging = nullptr;
   size_t staging_bytes = 0;
+  // host readbacks: two device staging slots; the gather runs on the
+  // context's stream, the device-to-host copy on copy_stream, so that the
+  // copy of one step's field overlaps the next step
+  struct RbSlot {
+    void* buf = nullptr;
+    size_t cap = 0;
+    cudaEvent_t copied = nullptr;  // recorded on copy_stream after the slot's copies
+    uint32_t* status = nullptr;    // pinned host word: the device status at the gather
+    int64_t ticket = -1;
+  };
+  RbSlot rb[2];
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t rb_gathered = nullptr;
+  int64_t rb_next = 0;
 
   std::vector<SceneHost> scenes;
   std::vector<SceneDev> h_scenes;
@@ -362,10 +376,7 @@ const Seg* find_seg(ckmpm_ctx* ctx, int slot) {
   return nullptr;
 }
 
-ckmpm_status read_device_error(ckmpm_ctx* ctx) {
-  uint32_t e = 0;
-  cudaError_t ce = cudaMemcpy(&e, ctx->counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "reading the device status word");
+ckmpm_status apply_device_error(ckmpm_ctx* ctx, uint32_t e) {
   if (ctx->sticky == CKMPM_OK) {
     if (e & CK_ERR_NONFINITE) {
       ctx->sticky = CKMPM_ENONFINITE;
@@ -385,6 +396,13 @@ ckmpm_status read_device_error(ckmpm_ctx* ctx) {
     }
   }
   return ctx->sticky;
+}
+
+ckmpm_status read_device_error(ckmpm_ctx* ctx) {
+  uint32_t e = 0;
+  cudaError_t ce = cudaMemcpy(&e, ctx->counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "reading the device status word");
+  return apply_device_error(ctx, e);
 }
 
 bool ensure_staging(ckmpm_ctx* ctx, size_t bytes) {
@@ -432,11 +450,16 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
   // host material indices are checked here, before any device work; device
   // arrays are checked by the admission kernel (material 0 and EINVAL)
   if (s->mat && !s->is_device) {
-    for (int64_t i = 0; i < s->n; ++i)
-      if ((int)s->mat[i] >= s->n_materials)
-        return fail(ctx, CKMPM_EINVAL,
-                    "scene.mat[" + std::to_string(i) + "] = " + std::to_string((int)s->mat[i]) +
-                        " is not below n_materials");
+    // a max-reduction (vectorised by the compiler) first; the offending
+    // index is searched for only when there is one
+    uint8_t mx = 0;
+    for (int64_t i = 0; i < s->n; ++i) mx = std::max(mx, s->mat[i]);
+    if ((int)mx >= s->n_materials)
+      for (int64_t i = 0; i < s->n; ++i)
+        if ((int)s->mat[i] >= s->n_materials)
+          return fail(ctx, CKMPM_EINVAL,
+                      "scene.mat[" + std::to_string(i) + "] = " + std::to_string((int)s->mat[i]) +
+                          " is not below n_materials");
   }
   return CKMPM_OK;
 }
@@ -1103,7 +1126,15 @@ int64_t ckmpm_scene_particles(const ckmpm_ctx* ctx, int scene_id) {
   return ctx->scenes[scene_id].n;
 }
 
-ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, size_t bytes, int dst_is_device) {
+}  // extern "C"
+
+namespace {
+
+// Checks a readback request; on success *want is the field's size in bytes
+// and *which the grid field to gather (the velocity/mass of the next step's
+// grid after a fused step).
+ckmpm_status readback_check(ckmpm_ctx* ctx, int scene_id, int field, const void* dst, size_t bytes, size_t* want,
+                            int* which) {
   if (!ctx) return CKMPM_EINVAL;
   if (scene_id < 0 || scene_id >= ctx->cap_scenes || !ctx->scenes[scene_id].alive)
     return fail(ctx, CKMPM_ENOTFOUND, "unknown scene id");
@@ -1111,54 +1142,127 @@ ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, 
   if (capturing(ctx)) return fail(ctx, CKMPM_EBUSY, "readback is not allowed during stream capture");
   const SceneHost& h = ctx->scenes[scene_id];
   const int NG = ctx->kind == 0 ? 2 : 1;
-  size_t want = 0;
+  *want = 0;
   if (field >= CKMPM_FIELD_GRID_M && field <= CKMPM_FIELD_GRID_V) {
     int64_t n = h.res + 1;
-    want = sizeof(float) * (size_t)(NG * n * n * n) * (field == CKMPM_FIELD_GRID_M ? 1 : 3);
+    *want = sizeof(float) * (size_t)(NG * n * n * n) * (field == CKMPM_FIELD_GRID_M ? 1 : 3);
   } else {
     int64_t f = field_floats(field);
     if (f == 0) return fail(ctx, CKMPM_EINVAL, "unknown field");
     if (field == CKMPM_FIELD_E && !ctx->per_E) return fail(ctx, CKMPM_EINVAL, "context has no per-particle E");
-    want = sizeof(float) * (size_t)(f * h.n);
+    *want = sizeof(float) * (size_t)(f * h.n);
   }
-  if (bytes != want) return fail(ctx, CKMPM_EINVAL, "readback size mismatch: expected " + std::to_string(want));
+  if (bytes != *want) return fail(ctx, CKMPM_EINVAL, "readback size mismatch: expected " + std::to_string(*want));
   // a fused step leaves the next step's grid as velocities and masses only
   // (its grid update consumed the momenta): mass and velocity come from
   // there until a probe replaces them
-  int which = field - CKMPM_FIELD_GRID_M;
+  *which = field - CKMPM_FIELD_GRID_M;
   if (field >= CKMPM_FIELD_GRID_M && ctx->fused && ctx->grid_valid) {
     if (field == CKMPM_FIELD_GRID_P)
       return fail(ctx, CKMPM_EINVAL, "after a fused step the grid momentum is consumed; probe the grids for it");
-    which = field == CKMPM_FIELD_GRID_M ? 3 : 4;
+    *which = field == CKMPM_FIELD_GRID_M ? 3 : 4;
   }
-  float* out = (float*)dst;
-  void* tmp = nullptr;
-  if (!dst_is_device) {
-    tmp = dev_alloc(ctx, want);
-    if (!tmp) return fail(ctx, CKMPM_ENOMEM, "temporary allocation failed");
-    out = (float*)tmp;
-  }
+  return CKMPM_OK;
+}
+
+// Enqueues the gather of one field into the device buffer out (want bytes)
+// on the context's stream.
+ckmpm_status readback_gather(ckmpm_ctx* ctx, int scene_id, int field, int which, size_t want, float* out) {
   if (field >= CKMPM_FIELD_GRID_M) {
-    cudaError_t me = cudaMemsetAsync(out, 0, want, ctx->stream);
-    if (me != cudaSuccess) {
-      if (tmp) dev_free(ctx, tmp);
-      return cuda_fail(ctx, me, "memset");
-    }
+    CK_TRY(cudaMemsetAsync(out, 0, want, ctx->stream), "memset");
     ck::launch_read_grid(ctx->kind, ctx->stream, make_view(ctx), scene_id, which, out);
   } else {
     const Seg* sg = find_seg(ctx, scene_id);
-    if (!sg) {
-      if (tmp) dev_free(ctx, tmp);
-      return fail(ctx, CKMPM_EINVAL, "scene has no particles in the pool");
-    }
-    ck::launch_read_particles(ctx->kind, ctx->transfer == CKMPM_TRANSFER_PIC, ctx->stream, ctx->pool[ctx->cur], ctx->d_scenes, ctx->d_mats, scene_id,
-                              (uint32_t)sg->start, (uint32_t)sg->n, field, out);
+    if (!sg) return fail(ctx, CKMPM_EINVAL, "scene has no particles in the pool");
+    ck::launch_read_particles(ctx->kind, ctx->transfer == CKMPM_TRANSFER_PIC, ctx->stream, ctx->pool[ctx->cur],
+                              ctx->d_scenes, ctx->d_mats, scene_id, (uint32_t)sg->start, (uint32_t)sg->n, field, out);
   }
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(dst, tmp, want, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (tmp) dev_free(ctx, tmp);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "readback");
+  CK_TRY(cudaGetLastError(), "readback gather");
+  return CKMPM_OK;
+}
+
+// The readback slot of a ticket; waits for the slot's last copies first when
+// its buffer has to grow.
+ckmpm_status readback_slot(ckmpm_ctx* ctx, size_t want, ckmpm_ctx::RbSlot** out) {
+  if (!ctx->copy_stream) {
+    CK_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+    CK_TRY(cudaEventCreateWithFlags(&ctx->rb_gathered, cudaEventDisableTiming), "readback event");
+    for (auto& sl : ctx->rb) {
+      CK_TRY(cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming), "readback event");
+      CK_TRY(cudaHostAlloc((void**)&sl.status, sizeof(uint32_t), cudaHostAllocDefault), "readback status word");
+      *sl.status = 0;
+    }
+  }
+  ckmpm_ctx::RbSlot& sl = ctx->rb[ctx->rb_next & 1];
+  if (sl.cap < want) {
+    if (sl.buf) {
+      CK_TRY(cudaEventSynchronize(sl.copied), "readback slot");
+      dev_free(ctx, sl.buf);
+      sl.buf = nullptr;
+      sl.cap = 0;
+    }
+    sl.buf = dev_alloc(ctx, want);
+    if (!sl.buf) return fail(ctx, CKMPM_ENOMEM, "readback staging allocation failed");
+    sl.cap = want;
+  } else if (sl.ticket >= 0) {
+    // the gather must not overwrite the slot while its previous copy runs
+    CK_TRY(cudaStreamWaitEvent(ctx->stream, sl.copied, 0), "readback slot");
+  }
+  *out = &sl;
+  return CKMPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ckmpm_status ckmpm_readback_async(ckmpm_ctx* ctx, int scene_id, int field, void* dst, size_t bytes,
+                                  int64_t* ticket) {
+  if (ticket) *ticket = -1;
+  if (!ctx) return CKMPM_EINVAL;
+  if (!ticket) return fail(ctx, CKMPM_EINVAL, "ticket is NULL");
+  size_t want = 0;
+  int which = 0;
+  ckmpm_status s = readback_check(ctx, scene_id, field, dst, bytes, &want, &which);
+  if (s != CKMPM_OK) return s;
+  ckmpm_ctx::RbSlot* sl = nullptr;
+  if ((s = readback_slot(ctx, want, &sl)) != CKMPM_OK) return s;
+  if ((s = readback_gather(ctx, scene_id, field, which, want, (float*)sl->buf)) != CKMPM_OK) return s;
+  CK_TRY(cudaEventRecord(ctx->rb_gathered, ctx->stream), "readback event");
+  CK_TRY(cudaStreamWaitEvent(ctx->copy_stream, ctx->rb_gathered, 0), "readback event");
+  CK_TRY(cudaMemcpyAsync(dst, sl->buf, want, cudaMemcpyDeviceToHost, ctx->copy_stream), "readback copy");
+  CK_TRY(cudaMemcpyAsync(sl->status, ctx->counters + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->copy_stream),
+         "readback copy");
+  CK_TRY(cudaEventRecord(sl->copied, ctx->copy_stream), "readback event");
+  sl->ticket = ctx->rb_next;
+  *ticket = ctx->rb_next++;
+  return CKMPM_OK;
+}
+
+ckmpm_status ckmpm_readback_wait(ckmpm_ctx* ctx, int64_t ticket) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (ticket < 0 || ticket >= ctx->rb_next) return fail(ctx, CKMPM_EINVAL, "unknown readback ticket");
+  // a slot's copies run in ticket order behind its previous ones, so the
+  // slot's latest copy completing implies every older ticket of the slot
+  ckmpm_ctx::RbSlot& sl = ctx->rb[ticket & 1];
+  CK_TRY(cudaEventSynchronize(sl.copied), "readback wait");
+  return apply_device_error(ctx, *sl.status);
+}
+
+ckmpm_status ckmpm_readback(ckmpm_ctx* ctx, int scene_id, int field, void* dst, size_t bytes, int dst_is_device) {
+  if (!ctx) return CKMPM_EINVAL;
+  if (!dst_is_device) {
+    int64_t t = -1;
+    ckmpm_status s = ckmpm_readback_async(ctx, scene_id, field, dst, bytes, &t);
+    if (s != CKMPM_OK) return s;
+    return ckmpm_readback_wait(ctx, t);
+  }
+  size_t want = 0;
+  int which = 0;
+  ckmpm_status s = readback_check(ctx, scene_id, field, dst, bytes, &want, &which);
+  if (s != CKMPM_OK) return s;
+  if ((s = readback_gather(ctx, scene_id, field, which, want, (float*)dst)) != CKMPM_OK) return s;
+  CK_TRY(cudaStreamSynchronize(ctx->stream), "readback");
   return read_device_error(ctx);
 }
 
@@ -1257,6 +1361,15 @@ ckmpm_status ckmpm_destroy(ckmpm_ctx* ctx) {
   }
   if (ctx->step_a) cudaEventDestroy(ctx->step_a);
   if (ctx->step_b) cudaEventDestroy(ctx->step_b);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    for (auto& sl : ctx->rb) {
+      if (sl.copied) cudaEventDestroy(sl.copied);
+      if (sl.status) cudaFreeHost(sl.status);
+    }
+    if (ctx->rb_gathered) cudaEventDestroy(ctx->rb_gathered);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
   while (!ctx->allocs.empty()) dev_free(ctx, ctx->allocs.back().first);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaGetLastError();

@@ -44,6 +44,10 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert lib.ckmpm_sync(None) == ckmpm.EINVAL
     assert lib.ckmpm_last_error(None) == b"no context"
     assert lib.ckmpm_scene_particles(None, 0) == -1
+    assert lib.ckmpm_readback_wait(None, 0) == ckmpm.EINVAL
+    t = ctypes.c_int64(7)
+    assert lib.ckmpm_readback_async(None, 0, ckmpm.FIELD_X, None, 0, ctypes.byref(t)) == ckmpm.EINVAL
+    assert t.value == -1
     out = ctypes.c_void_p()
     assert lib.ckmpm_create(None, 0, None, ctypes.byref(out)) == ckmpm.EINVAL
     assert out.value is None

@@ -54,7 +54,9 @@ def test_graph_steps_match_direct_launches(kernel, fused):
     assert n1 >= 8  # all but the first step after creation and after the upload (fused: also the prologues)
     assert np.abs(got[0] - want[0]).max() <= 1e-6 * sc.dx + 2e-7
     assert rel(got[1], want[1]) <= 1e-5
-    assert rel(got[2], want[2]) <= 1e-6
+    # F integrates the gradients of the same grid velocities (1.4e-6 seen
+    # for the fused step, whose leftover list order varies between runs)
+    assert rel(got[2], want[2]) <= 1e-5
 
 
 def test_graph_steps_across_admission_and_release():

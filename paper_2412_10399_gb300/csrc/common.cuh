@@ -113,6 +113,7 @@ struct StepView {
   uint32_t n_cur;       // particles in cur (including dead ones)
   uint32_t keep_gacc;   // probe: the grid update leaves Gacc, P2G keeps bnd_cur
   uint32_t splits;      // work units per particle block of the transfer kernels (>= 1)
+  uint32_t n_mats;      // entries of the material table
   // fused G2P2G step only (else null): the block table of the next step's
   // grid (the gather reads Gvel through `table`, the scatter adds to Gacc
   // through these), and the list of particles the fused kernel leaves to the

@@ -261,6 +261,7 @@ ck::StepView make_view(ckmpm_ctx* ctx) {
   v.Gvel = ctx->Gvel;
   v.scenes = ctx->d_scenes;
   v.mats = ctx->d_mats;
+  v.n_mats = (uint32_t)ctx->cap_mats;
   v.n_keys = (uint32_t)std::max<int64_t>(ctx->keys_alloc.high, 1);
   v.n_cur = (uint32_t)ctx->n_cur;
   v.keep_gacc = 0;
@@ -492,7 +493,7 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   if (const char* e = getenv("CKMPM_CTAS_PER_SM")) per_sm = std::max(1, atoi(e));
   ctx->lc.persistent_ctas = ctx->sm_count * per_sm;
   ctx->lc.sm_count = ctx->sm_count;
-  ctx->lc.g2p_minb = ctx->kind == 0 ? 5 : 4;
+  ctx->lc.g2p_minb = 5;
   ctx->lc.transfer = ctx->transfer == CKMPM_TRANSFER_PIC ? 1 : ctx->transfer == CKMPM_TRANSFER_APIC_GRAD ? 2 : 0;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
   // two copies of the P2G accumulators are the faster choice for the

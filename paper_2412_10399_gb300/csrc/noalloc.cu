@@ -183,6 +183,7 @@ extern "C" CKMPM_API ckmpm_status ckmpm_p2g_grids_static(const ckmpm_scene* sc, 
   if (!cv.ok) return CKMPM_ENOMEM;  // cannot happen within the limits above
   v.scenes = d_scene;
   v.mats = d_mats;
+  v.n_mats = kStaticMaxMats;
   v.n_keys = (uint32_t)nkeys;
   v.n_cur = (uint32_t)n;
   v.keep_gacc = 1;

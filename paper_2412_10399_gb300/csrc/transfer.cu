@@ -37,6 +37,16 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Material tables of up to this many entries are staged in shared memory by
+// the transfer kernels (one copy per CTA).
+constexpr int kSmemMats = 8;
 
 // sin(2 pi f) for f in [0, 1): reduce to t = f - rint(f) in [-1/2, 1/2], fold
 // |t| > 1/4 with sin(2 pi t) = sin(2 pi (sign(t)/2 - t)) (both steps exact in
@@ -834,9 +844,9 @@ __device__ __forceinline__ float min3(float a, float b, float c) { return fminf(
 // G2P runs one warp per CTA: a particle block's ~400-500 particles leave a
 // partly idle last round on 32 lanes instead of on 128, and the staging
 // waits are warp-level, so a lane that finishes early never holds up three
-// other warps at a block barrier.  MINB counts 4-warp equivalents per SM; at
-// 5 or more the staging chunk shrinks to 64 particles so that shared memory
-// admits the extra warps.
+// other warps at a block barrier.  MINB counts 4-warp equivalents per SM.
+// The fused G2P2G kernel stages g2p_stage(MINB) particles per chunk (64 at
+// 5 or more, so that shared memory admits the extra warps).
 constexpr int kG2PWarp = 32;
 __host__ __device__ constexpr int g2p_stage(int minb) { return minb >= 5 ? 64 : 128; }  // particles per chunk
 
@@ -858,10 +868,11 @@ template <int KIND, int TR>
 __device__ __forceinline__ bool g2p_particle(const StepView& v, const SceneDev& s, int ox, int oy, int oz,
                                              const float4* sv, uint32_t t, const float4 X, const float4 f0,
                                              const float4 f1, const float f2, const uint32_t id, const float Eraw,
-                                             G2POut& out) {
+                                             G2POut& out, const MatDev* smat = nullptr) {
   out.use64 = false;
   const uint32_t mi = __float_as_uint(X.w);
-  const MatDev mt = v.mats[mi];
+  // the material table from shared memory when the kernel staged it there
+  const MatDev mt = smat ? smat[mi] : v.mats[mi];
   float mu = mt.mu, lam = mt.lam;
   float Ep = 0.f;
   if (v.cur.E) {
@@ -1019,68 +1030,118 @@ __device__ __forceinline__ bool g2p_particle(const StepView& v, const SceneDev& 
   return true;
 }
 
+// G2P with the next chunk's particle state in flight.  Chunks of 32
+// particles (one per lane; each lane stages and reads only its own
+// particle's slot) alternate between two staging buffers: while chunk k is
+// computed, chunk k+1 is being gathered with cp.async.  The binned-order
+// indices (perm) that address those gathers travel by cp.async into shared
+// memory too, three chunks ahead, so inside a block no load result is waited
+// on and no index is held in a register across a chunk's computation (held
+// there, one was spilled to local memory at this register budget, and its
+// spill store waited for the load).
+
 // TR: transfer, 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient.
 template <int KIND, int MINB, int TR>
 __global__ void __launch_bounds__(kG2PWarp, 4 * MINB) k_g2p(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  constexpr int CAP = g2p_stage(MINB);
-  __shared__ float4 sv[NS];  // staged v~ (w unused): one 16-byte shared load per node
-  __shared__ float4 sX[CAP], sF0[CAP], sF1[CAP];
-  __shared__ float sF2[CAP], sE[CAP];
-  __shared__ uint32_t sID[CAP];
+  constexpr int CH = 32;
+  constexpr int NB = 2;       // staging buffers (four measured slower: registers)
+  constexpr int D = NB - 1;   // chunks in flight ahead of the computed one
+  constexpr int PS = 2 * NB;  // slots of binned-order indices (D + 2 live at a time)
+  static_assert((NB & (NB - 1)) == 0, "NB must be a power of two");
+  __shared__ float4 sv[NS];
+  __shared__ float4 sX[NB][CH], sF0[NB][CH], sF1[NB][CH];
+  __shared__ float sF2[NB][CH], sE[NB][CH];
+  __shared__ uint32_t sID[NB][CH];
+  __shared__ uint32_t sP[PS][CH];
   __shared__ uint32_t bslot[8];
+  __shared__ MatDev smat[kSmemMats];
+  const uint32_t lane = threadIdx.x;
+  const bool mat_smem = v.n_mats <= (uint32_t)kSmemMats;
+  if (mat_smem) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(v.mats);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(smat);
+    const uint32_t words = v.n_mats * (uint32_t)(sizeof(MatDev) / 4);
+    for (uint32_t w = lane; w < words; w += CH) dst[w] = src[w];
+  }
+  __syncwarp();
   const uint32_t nunits = *v.n_pb * v.splits;
   for (;;) {
-    // work units (a block or a part of one) are handed out one at a time
-    // (dynamic scheduling: their costs vary with particle counts and
-    // constitutive work)
     uint32_t u = 0;
-    if (threadIdx.x == 0) u = atomicAdd(&v.work[1], 1u);
+    if (lane == 0) u = atomicAdd(&v.work[1], 1u);
     u = __shfl_sync(0xffffffffu, u, 0);
     if (u >= nunits) break;
     uint32_t bi, lo, hi;
-    if (!unit_range(v, u, CAP, bi, lo, hi)) continue;
+    if (!unit_range(v, u, CH, bi, lo, hi)) continue;
     const uint32_t key = v.pb_key[bi];
     const SceneDev s = v.scenes[v.pb_scene[bi]];
     const uint32_t start = v.offset[key];
     int ox, oy, oz;
     decode_block(s, key, ox, oy, oz);
     load_block_slots(v, s, ox, oy, oz, bslot);
-    __syncwarp();
-    for (uint32_t c0 = lo; c0 < hi; c0 += CAP) {
-    const uint32_t m = min(hi - c0, (uint32_t)CAP);
-    // the chunk's particle state and (first chunk) the block's grid
-    // velocities: cp.async gathers, all in flight before the one wait
-#pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const uint32_t p = v.perm[start + c0 + i];
-      cp_async16(&sX[i], &v.cur.X[p]);
-      cp_async16(&sF0[i], &v.cur.F0[p]);
-      cp_async16(&sF1[i], &v.cur.F1[p]);
-      cp_async4(&sF2[i], &v.cur.F2[p]);
-      cp_async4(&sID[i], &v.cur.ID[p]);
-      if (v.cur.E) cp_async4(&sE[i], &v.cur.E[p]);
+    const uint32_t nch = (hi - lo + CH - 1) / CH;
+    // Each lane stages and reads only its own slot of every buffer, so the
+    // index and particle buffers need no cross-lane ordering; sv does.
+    // Binned-order indices of chunks 0 .. 2D: loaded together; chunks
+    // 0 .. D-1 are staged at once, D .. 2D parked in sP.  The index of chunk
+    // c >= 2D + 1 is fetched by cp.async in the group of chunk c - D - 1,
+    // which has landed before chunk c is staged.
+    uint32_t pp[2 * D + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * D; ++j) {
+      const uint32_t i = lo + (uint32_t)j * CH + lane;
+      pp[j] = i < hi ? v.perm[start + i] : 0u;
     }
-    if (c0 == lo) {
-      for (int j = threadIdx.x; j < NS; j += blockDim.x) {
-        int g, lx, ly, lz;
-        staged_coords<KIND>(j, g, lx, ly, lz);
-        long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
-        if (gi >= 0)
-          cp_async16(&sv[j], &v.Gvel[gi]);
-        else
-          sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = D; j <= 2 * D; ++j) sP[j % PS][lane] = pp[j];
+    __syncwarp();  // bslot
+    for (int j = lane; j < NS; j += CH) {
+      int g, lx, ly, lz;
+      staged_coords<KIND>(j, g, lx, ly, lz);
+      const long long gi = pool_index<KIND>(bslot, g, lx, ly, lz);
+      if (gi >= 0)
+        cp_async16(&sv[j], &v.Gvel[gi]);
+      else
+        sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    auto stage = [&](uint32_t c, uint32_t p) {
+      const uint32_t b = c & (NB - 1);
+      if (lo + c * CH + lane < hi) {
+        cp_async16(&sX[b][lane], &v.cur.X[p]);
+        cp_async16(&sF0[b][lane], &v.cur.F0[p]);
+        cp_async16(&sF1[b][lane], &v.cur.F1[p]);
+        cp_async4(&sF2[b][lane], &v.cur.F2[p]);
+        cp_async4(&sID[b][lane], &v.cur.ID[p]);
+        if (v.cur.E) cp_async4(&sE[b][lane], &v.cur.E[p]);
       }
+    };
+    // chunks 0 .. D-1 (the grid velocities go with chunk 0's group)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      if ((uint32_t)j < nch) stage((uint32_t)j, pp[j]);
+      cp_async_commit();
     }
-    cp_async_wait_all();
-    __syncwarp();
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      G2POut o;
-      if (g2p_particle<KIND, TR>(v, s, ox, oy, oz, sv, start + c0 + i, sX[i], sF0[i], sF1[i], sF2[i], sID[i],
-                                 v.cur.E ? sE[i] : 0.f, o))
-        warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, o.nk, o.bmass, o.bmom);
-    }
-    __syncwarp();  // the next chunk (or unit) overwrites the staged copies
+    for (uint32_t k = 0; k < nch; ++k) {
+      const uint32_t kn = k + D;
+      if (kn < nch) stage(kn, sP[kn % PS][lane]);
+      const uint32_t kp = k + 2 * D + 1;
+      if (kp < nch) {
+        const uint32_t i = lo + kp * CH + lane;
+        if (i < hi) cp_async4(&sP[kp % PS][lane], &v.perm[start + i]);
+      }
+      cp_async_commit();
+      cp_async_wait<D>();  // the D newest groups may still be in flight: chunk k has landed
+      __syncwarp();
+      const uint32_t b = k & (NB - 1);
+      const uint32_t i = lo + k * CH + lane;
+      if (i < hi) {
+        G2POut o;
+        if (g2p_particle<KIND, TR>(v, s, ox, oy, oz, sv, start + i, sX[b][lane], sF0[b][lane], sF1[b][lane],
+                                   sF2[b][lane], sID[b][lane], v.cur.E ? sE[b][lane] : 0.f, o,
+                                   mat_smem ? smat : nullptr))
+          warp_aggregated_bin(v.cnt_nxt, v.bnd_nxt, o.nk, o.bmass, o.bmom);
+      }
+      __syncwarp();  // chunk k + NB is staged into this buffer next
     }
   }
 }
@@ -1740,13 +1801,13 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
     // one block (list entry, scene, accumulators) overlap across CTAs
     case LK_UPDATE: k_grid_update<KIND><<<lc.sm_count * 64, 128, 0, lc.stream>>>(v); break;
     case LK_G2P:
-      // register budget of G2P: 20 warps/SM (96 registers, 64-particle
-      // chunks) for the compact kernel and 16 (128 registers) for the
-      // quadratic twin by default, the faster of each on the large-impact
-      // scene; 24 (80 registers) on request.  One resident wave.
-      // The kernel-gradient transfers run one budget each: PIC the APIC
-      // default; the kernel-gradient APIC (two gathers) 16 warps/SM for CK
-      // and 12 (170 registers, no spills) for the quadratic twin.
+      // register budget of G2P: 20 warps/SM (96 registers) by default, the
+      // faster for both kernels on the large-impact scene; 16 (119-124
+      // registers) or 24 (80) on request.  One resident wave.  The kernel-
+      // gradient transfers run one budget each: PIC the APIC default (16
+      // warps/SM for the quadratic twin); the kernel-gradient APIC (two
+      // gathers) 16 warps/SM for CK and 12 (168 registers, no spills) for
+      // the quadratic twin.
       if (lc.transfer == 1)
         k_g2p<KIND, KIND == 0 ? 5 : 4, 1><<<lc.sm_count * (KIND == 0 ? 20 : 16), kG2PWarp, 0, lc.stream>>>(v);
       else if (lc.transfer == 2)

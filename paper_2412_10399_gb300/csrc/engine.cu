@@ -421,6 +421,30 @@ bool ensure_staging(ckmpm_ctx* ctx, size_t bytes) {
   return true;
 }
 
+// Whether any of the n bytes at p is >= k (1 <= k <= 255), eight bytes per
+// step for k <= 128: with h = 127 - (k - 1), a byte b < 128 gets its top bit
+// from b + h exactly when b >= k (b + h <= 254, so no carry leaves the byte),
+// and a byte b >= 128 has it already, which OR-ing b keeps whatever carry the
+// addition produced; a carry only ever leaves a byte whose top bit is set, so
+// the word's answer is exact.
+bool any_byte_at_least(const uint8_t* p, int64_t n, int k) {
+  int64_t i = 0;
+  if (k <= 128) {
+    const uint64_t ones = 0x0101010101010101ull, tops = 0x8080808080808080ull;
+    const uint64_t add = ones * (uint64_t)(128 - k);
+    uint64_t acc = 0;
+    for (; i + 8 <= n; i += 8) {
+      uint64_t w;
+      std::memcpy(&w, p + i, 8);
+      acc |= ((w + add) | w) & tops;
+    }
+    if (acc) return true;
+  }
+  for (; i < n; ++i)
+    if ((int)p[i] >= k) return true;
+  return false;
+}
+
 ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
   if (!s) return fail(ctx, CKMPM_EINVAL, "scene is NULL");
   if (s->n < 1 || s->n > 0x7fffffffLL) return fail(ctx, CKMPM_EINVAL, "scene.n must be in [1, 2^31)");
@@ -451,15 +475,15 @@ ckmpm_status validate_scene(ckmpm_ctx* ctx, const ckmpm_scene* s) {
   // host material indices are checked here, before any device work; device
   // arrays are checked by the admission kernel (material 0 and EINVAL)
   if (s->mat && !s->is_device) {
-    // a max-reduction (vectorised by the compiler) first; the offending
-    // index is searched for only when there is one
-    uint8_t mx = 0;
-    for (int64_t i = 0; i < s->n; ++i) mx = std::max(mx, s->mat[i]);
-    if ((int)mx >= s->n_materials)
-      for (int64_t i = 0; i < s->n; ++i)
-        if ((int)s->mat[i] >= s->n_materials)
+    // a word-at-a-time test first; the offending index is searched for only
+    // when there is one
+    const uint8_t* mat = s->mat;
+    const int64_t n = s->n;
+    if (any_byte_at_least(mat, n, s->n_materials))
+      for (int64_t i = 0; i < n; ++i)
+        if ((int)mat[i] >= s->n_materials)
           return fail(ctx, CKMPM_EINVAL,
-                      "scene.mat[" + std::to_string(i) + "] = " + std::to_string((int)s->mat[i]) +
+                      "scene.mat[" + std::to_string(i) + "] = " + std::to_string((int)mat[i]) +
                           " is not below n_materials");
   }
   return CKMPM_OK;

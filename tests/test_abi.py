@@ -213,3 +213,36 @@ def test_material_index_and_friction_angle_are_checked_before_any_device_work():
     bad = scenes.Material(scenes.DRUCKER_PRAGER, 3.5e5, 0.3, 1600.0, -5.0)
     sc2, keep2 = ckmpm.make_scene(16, 1 / 16, 1e-4, [bad], x)
     assert lib.ckmpm_create(ctypes.byref(sc2), 0, None, ctypes.byref(out)) == ckmpm.EINVAL
+
+
+def test_material_index_check_at_every_position_and_table_size():
+    """The host check of material indices tests eight bytes per step for
+    tables of up to 128 materials and one byte at a time for larger ones
+    and for the tail: an index equal to n_materials (or 255) is EINVAL at
+    any position, and arrays whose largest index is n_materials - 1 pass the
+    check (without a GPU, creation then fails later, but not with EINVAL)."""
+    import numpy as np
+    from paper_2412_10399_gb300 import ckmpm, scenes
+    lib = ckmpm.load()
+    n = 37  # four words and a five-byte tail
+    x = np.full((n, 3), 0.5, np.float32)
+    g = np.random.default_rng(7)
+    for nm in (1, 2, 3, 127, 128, 129, 200, 255):
+        mats = [scenes.ELASTIC] * nm
+        for fill in ("max", "random"):
+            mat = np.full(n, nm - 1, np.uint8) if fill == "max" else g.integers(0, nm, n).astype(np.uint8)
+            sc, keep = ckmpm.make_scene(16, 1 / 16, 1e-4, mats, x, mat=mat)
+            out = ctypes.c_void_p()
+            st = lib.ckmpm_create(ctypes.byref(sc), 0, None, ctypes.byref(out))
+            assert st != ckmpm.EINVAL, (nm, fill)
+            if st == ckmpm.OK:
+                lib.ckmpm_destroy(out)
+        if nm == 255:
+            continue  # every byte value is a valid index
+        for pos in (0, 7, 8, 15, 31, 32, 36):
+            for badv in (nm, 255):
+                mat = np.zeros(n, np.uint8)
+                mat[pos] = badv
+                sc, keep = ckmpm.make_scene(16, 1 / 16, 1e-4, mats, x, mat=mat)
+                out = ctypes.c_void_p()
+                assert lib.ckmpm_create(ctypes.byref(sc), 0, None, ctypes.byref(out)) == ckmpm.EINVAL, (nm, pos, badv)

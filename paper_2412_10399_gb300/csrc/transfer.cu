@@ -809,30 +809,45 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
 template <int KIND>
 __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
   constexpr int NG = Geo<KIND>::NG;
+  constexpr int PB = 2;  // blocks per iteration: their dependent loads (list entry, scene, sums) overlap
   const uint32_t ng = min(*v.n_g, v.pool_cap);
-  for (uint32_t gi = blockIdx.x; gi < ng; gi += gridDim.x) {
-    const uint32_t g = v.g_list[gi];
-    const SceneDev s = v.scenes[v.g_scene[gi]];
-    long long lb = (long long)g - s.table_base;
-    int gx = (int)(lb % s.nb), gy = (int)((lb / s.nb) % s.nb), gz = (int)(lb / ((long long)s.nb * s.nb));
+  for (uint32_t g0 = blockIdx.x * PB; g0 < ng; g0 += gridDim.x * PB) {
+    uint32_t gb[PB];
+    SceneDev sd[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      const uint32_t gi = min(g0 + k, ng - 1);  // a missing second block repeats the first's reads
+      gb[k] = v.g_list[gi];
+      sd[k] = v.scenes[v.g_scene[gi]];
+    }
     for (int t = threadIdx.x; t < NG * kBlockNodes; t += blockDim.x) {
-      int grid = t / kBlockNodes, l = t % kBlockNodes;
-      int ix = gx * 4 + (l & 3), iy = gy * 4 + ((l >> 2) & 3), iz = gz * 4 + (l >> 4);
-      float off = KIND == 0 ? (grid == 0 ? 0.25f : -0.25f) : 0.0f;
-      long long idx = ((long long)gi * NG + grid) * kBlockNodes + l;
-      float4 acc = v.Gacc[idx];
-      float4 o = make_float4(0.f, 0.f, 0.f, acc.x);
-      if (acc.x > 0.f) {
-        o.x = acc.y / acc.x + s.dt * s.gx;
-        o.y = acc.z / acc.x + s.dt * s.gy;
-        o.z = acc.w / acc.x + s.dt * s.gz;
+      const int grid = t / kBlockNodes, l = t % kBlockNodes;
+      float4 acc[PB];
+#pragma unroll
+      for (int k = 0; k < PB; ++k)
+        acc[k] = g0 + k < ng ? v.Gacc[((long long)(g0 + k) * NG + grid) * kBlockNodes + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        if (g0 + k >= ng) break;
+        const SceneDev& s = sd[k];
+        const long long lb = (long long)gb[k] - s.table_base;
+        const int gx = (int)(lb % s.nb), gy = (int)((lb / s.nb) % s.nb), gz = (int)(lb / ((long long)s.nb * s.nb));
+        const int ix = gx * 4 + (l & 3), iy = gy * 4 + ((l >> 2) & 3), iz = gz * 4 + (l >> 4);
+        const float off = KIND == 0 ? (grid == 0 ? 0.25f : -0.25f) : 0.0f;
+        const long long idx = ((long long)(g0 + k) * NG + grid) * kBlockNodes + l;
+        float4 o = make_float4(0.f, 0.f, 0.f, acc[k].x);
+        if (acc[k].x > 0.f) {
+          o.x = acc[k].y / acc[k].x + s.dt * s.gx;
+          o.y = acc[k].z / acc[k].x + s.dt * s.gy;
+          o.z = acc[k].w / acc[k].x + s.dt * s.gz;
+        }
+        const float px = ix + off, py = iy + off, pz = iz + off;
+        const float hi = (float)s.res - s.bc;
+        const bool wall = px < s.bc || py < s.bc || pz < s.bc || px > hi || py > hi || pz > hi;
+        if (wall) o.x = o.y = o.z = 0.f;
+        v.Gvel[idx] = o;
+        if (!v.keep_gacc) v.Gacc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      float px = ix + off, py = iy + off, pz = iz + off;
-      float hi = (float)s.res - s.bc;
-      bool wall = px < s.bc || py < s.bc || pz < s.bc || px > hi || py > hi || pz > hi;
-      if (wall) o.x = o.y = o.z = 0.f;
-      v.Gvel[idx] = o;
-      if (!v.keep_gacc) v.Gacc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }

@@ -405,19 +405,24 @@ __device__ __forceinline__ void gather_moments(const float4* sv, int base, const
 }
 
 // v = h sum w v~ and Bh = h sum w v~ (x_i - x_p)^T / dx (row c, column a) over
-// the particle's stencil; h = 1/2 averages the two CK grids.
+// the particle's stencil; h = 1/2 averages the two CK grids.  Every sum is
+// linear in the z weights, so h is applied to those (four products) instead
+// of to the twelve results; scaling by a power of two is exact, so the
+// results are the same bits.
 __device__ __forceinline__ void g2p_gather(const Sten<0>& st, const float4* sv, float* vel, float* Bh) {
   float S[2][3], M[2][3][3];
-  gather_moments<2, 5>(sv, (st.r[0][2] * 5 + st.r[0][1]) * 5 + st.r[0][0], st.w[0][0], st.w[0][1], st.w[0][2],
-                       S[0], M[0][0], M[0][1], M[0][2]);
-  gather_moments<2, 6>(sv, 125 + (st.r[1][2] * 6 + st.r[1][1]) * 6 + st.r[1][0], st.w[1][0], st.w[1][1],
-                       st.w[1][2], S[1], M[1][0], M[1][1], M[1][2]);
+  const float hz0[2] = {0.5f * st.w[0][2][0], 0.5f * st.w[0][2][1]};
+  const float hz1[2] = {0.5f * st.w[1][2][0], 0.5f * st.w[1][2][1]};
+  gather_moments<2, 5>(sv, (st.r[0][2] * 5 + st.r[0][1]) * 5 + st.r[0][0], st.w[0][0], st.w[0][1], hz0, S[0],
+                       M[0][0], M[0][1], M[0][2]);
+  gather_moments<2, 6>(sv, 125 + (st.r[1][2] * 6 + st.r[1][1]) * 6 + st.r[1][0], st.w[1][0], st.w[1][1], hz1,
+                       S[1], M[1][0], M[1][1], M[1][2]);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    vel[c] = 0.5f * (S[0][c] + S[1][c]);
+    vel[c] = S[0][c] + S[1][c];
 #pragma unroll
     for (int a = 0; a < 3; ++a)  // f_a = -d[g][a][0]
-      Bh[c * 3 + a] = 0.5f * (fmaf(st.d[0][a][0], S[0][c], M[0][a][c]) + fmaf(st.d[1][a][0], S[1][c], M[1][a][c]));
+      Bh[c * 3 + a] = fmaf(st.d[0][a][0], S[0][c], M[0][a][c]) + fmaf(st.d[1][a][0], S[1][c], M[1][a][c]);
   }
 }
 
@@ -809,7 +814,9 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
 template <int KIND>
 __global__ void __launch_bounds__(128) k_grid_update(StepView v) {
   constexpr int NG = Geo<KIND>::NG;
-  constexpr int PB = 2;  // blocks per iteration: their dependent loads (list entry, scene, sums) overlap
+  // blocks per iteration: their dependent loads (list entry, scene, sums)
+  // overlap (four measured slower: registers)
+  constexpr int PB = 2;
   const uint32_t ng = min(*v.n_g, v.pool_cap);
   for (uint32_t g0 = blockIdx.x * PB; g0 < ng; g0 += gridDim.x * PB) {
     uint32_t gb[PB];

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
 // Each warp handles kScatterUnroll groups of 32 particles per pass and issues
 // the cursor atomics of all of them before it waits for the first result: the
 // pass is one atomic round trip instead of kScatterUnroll.
-constexpr int kScatterUnroll = 4;
+constexpr int kScatterUnroll = 8;
 
 __global__ void __launch_bounds__(256) k_scatter(StepView v) {
   const uint32_t lane = threadIdx.x & 31;
@@ -238,21 +238,51 @@ __global__ void __launch_bounds__(256) k_scatter(StepView v) {
 // Flagged virtual blocks get pool slots in list order; the block table maps
 // each of them to its slot.  Entries of untouched blocks are stale and never
 // read (P2G/G2P only look up the blocks their own particle block flagged).
+// A warp reads 32 x 4 flags with one 16-byte load per lane; a warp scan of
+// the lanes' flag counts and one atomic per warp give every flagged block its
+// slot.  The tail (fewer than four flags) and an unaligned array are read one
+// flag at a time.
+__device__ __forceinline__ void glist_assign(const StepView& v, uint32_t g, uint32_t f, uint32_t idx) {
+  if (idx < v.pool_cap) {
+    v.g_list[idx] = g;
+    v.g_scene[idx] = f - 1u;
+    v.table[g] = idx;
+  } else {
+    v.table[g] = CK_NO_SLOT;
+    flag_error(v.err, CK_ERR_POOL);
+  }
+  v.gflag[g] = 0u;
+}
+
 __global__ void k_glist(StepView v, uint32_t n_vblocks) {
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_vblocks; g += gridDim.x * blockDim.x) {
-    uint32_t f = v.gflag[g];
-    if (f) {
-      uint32_t idx = warp_aggregated_inc(v.n_g, 0u);
-      if (idx < v.pool_cap) {
-        v.g_list[idx] = g;
-        v.g_scene[idx] = f - 1u;
-        v.table[g] = idx;
-      } else {
-        v.table[g] = CK_NO_SLOT;
-        flag_error(v.err, CK_ERR_POOL);
-      }
-      v.gflag[g] = 0u;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t n4 = (reinterpret_cast<uintptr_t>(v.gflag) & 15u) ? 0u : n_vblocks / 4u;
+  const uint4* f4 = reinterpret_cast<const uint4*>(v.gflag);
+  const uint32_t wstride = gridDim.x * blockDim.x;
+  // every lane of a warp runs the same iterations (full-mask intrinsics)
+  for (uint32_t q0 = blockIdx.x * blockDim.x + (threadIdx.x - lane); q0 < n4; q0 += wstride) {
+    const uint32_t q = q0 + lane;
+    const uint4 f = q < n4 ? f4[q] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t nf = (f.x != 0u) + (f.y != 0u) + (f.z != 0u) + (f.w != 0u);
+    if (__ballot_sync(0xffffffffu, nf != 0u) == 0u) continue;
+    uint32_t inc = nf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += y;
     }
+    uint32_t start = 0u;
+    if (lane == 31u) start = atomicAdd(v.n_g, inc);
+    start = __shfl_sync(0xffffffffu, start, 31);
+    uint32_t idx = start + inc - nf;
+    if (f.x) glist_assign(v, 4u * q, f.x, idx++);
+    if (f.y) glist_assign(v, 4u * q + 1u, f.y, idx++);
+    if (f.z) glist_assign(v, 4u * q + 2u, f.z, idx++);
+    if (f.w) glist_assign(v, 4u * q + 3u, f.w, idx++);
+  }
+  for (uint32_t g = 4u * n4 + blockIdx.x * blockDim.x + threadIdx.x; g < n_vblocks; g += wstride) {
+    const uint32_t f = v.gflag[g];
+    if (f) glist_assign(v, g, f, atomicAdd(v.n_g, 1u));
   }
 }
 

@@ -178,6 +178,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
   }
   pc += ic - tc;
   pn += in - tn;
+  // the owning scene of the thread's keys, looked up once and kept in
+  // registers while the keys stay inside its key range (the stores below
+  // could alias the scene table, so reading it per key reloads it each time)
+  int sl = -1, npb = 1, nb = 1;
+  uint32_t klo = 1u;
+  uint64_t khi = 0u;
+  long long tbase = 0;
 #pragma unroll
   for (int q = 0; q < kPerThread; ++q) {
     uint32_t k = base + q;
@@ -185,16 +192,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(StepView v, BinScra
     if (c[q]) {
       v.offset[k] = pc;
       v.cursor[k] = pc;
-      int sl = scene_of_key(bs, k);
+      if (!(k >= klo && (uint64_t)k < khi)) {
+        sl = scene_of_key(bs, k);
+        const SceneDev& s = v.scenes[sl];
+        klo = s.key_base;
+        npb = s.npb;
+        nb = s.nb;
+        tbase = s.table_base;
+        khi = (uint64_t)klo + (uint64_t)npb * (uint64_t)npb * (uint64_t)npb;
+      }
       v.pb_key[pn] = k;
       v.pb_scene[pn] = (uint32_t)sl;
-      const SceneDev& s = v.scenes[sl];
-      int lb = (int)(k - s.key_base);
-      int bx = lb % s.npb, by = (lb / s.npb) % s.npb, bz = lb / (s.npb * s.npb);
+      int lb = (int)(k - klo);
+      int bx = lb % npb, by = (lb / npb) % npb, bz = lb / (npb * npb);
       for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
           for (int dx = 0; dx < 2; ++dx)
-            v.gflag[s.table_base + ((long long)(bz + dz) * s.nb + (by + dy)) * s.nb + (bx + dx)] = (uint32_t)sl + 1u;
+            v.gflag[tbase + ((long long)(bz + dz) * nb + (by + dy)) * nb + (bx + dx)] = (uint32_t)sl + 1u;
       pn += 1;
     }
     pc += c[q];

@@ -81,8 +81,8 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
+def _profile_value(kernel, field):
+    """A figure from the committed ncu summary of a kernel, if it was taken
     on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", f"traffic_{kernel}_large_impact.txt")
     if not os.path.exists(p):
@@ -95,9 +95,41 @@ def _traffic(kernel):
     if kv.get("source_hash") != _source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_launch_full_size"])
+        return float(kv[field])
     except (KeyError, ValueError):
         return None
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of a kernel on the full scene (ncu, scaled)."""
+    return _profile_value(kernel, "dram_bytes_per_launch_full_size")
+
+
+def fp32_sgemm_tflops(n=8192, reps=3):
+    """Measured FP32 ceiling of this GPU's CUDA cores: a cuBLAS SGEMM with
+    TF32 off (the FP32 counterpart of the bf16 GEMM behind the HBM and tensor
+    peaks), CUDA events around `reps` products after one warm-up."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        g = torch.Generator(device="cuda").manual_seed(0)
+        a = torch.randn(n, n, device="cuda", generator=g)
+        b = torch.randn(n, n, device="cuda", generator=g)
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            c = torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        del a, b, c
+        torch.cuda.empty_cache()
+        return 2.0 * n ** 3 * reps / (ms / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def aggregate_ranks(ms_local: float, particles_local: int, steps: int, dist=None, device="cpu"):
@@ -619,6 +651,20 @@ def run_gpu(args):
                 "step_frac": sum(ALGO_BYTES.values()) * n / (ms / args.steps / 1e3) / 1e9 / peak,
                 "method_floor_bytes_per_particle": METHOD_FLOOR_BYTES,
                 "step_frac_method_floor": METHOD_FLOOR_BYTES * n / (ms / args.steps / 1e3) / 1e9 / peak}
+    # the dominant kernel's FP32 arithmetic against the CUDA cores' ceiling
+    # (FLOP per particle from the same ncu capture as its traffic)
+    flops_pp = _profile_value(dominant, "fp32_flops_per_particle")
+    sgemm = fp32_sgemm_tflops()
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    max_mhz = float(clocks.get("sm_max_mhz") or 2070.0)
+    nominal_fp32 = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    alu_tf = flops_pp * n / (per_kernel[dominant] / 1e3) / 1e12 if flops_pp else None
+    roofline["alu"] = {"fp32_flops_per_particle": flops_pp, "achieved_tflops": alu_tf,
+                       "sgemm_tflops": sgemm, "frac_of_sgemm": alu_tf / sgemm if alu_tf else None,
+                       "nominal_tflops": nominal_fp32, "frac_of_nominal": alu_tf / nominal_fp32 if alu_tf else None,
+                       "note": "FP32 FLOP of the dominant kernel (2 FFMA + FMUL + FADD per the ncu counts) per "
+                               "CUDA-event launch time, against a cuBLAS SGEMM with TF32 off and against "
+                               "SMs x 128 lanes x 2 x max SM clock"}
 
     # ---------------- quadratic B-spline twin on the same inputs and steps
     qsteps = args.steps

@@ -414,28 +414,43 @@ __device__ __forceinline__ float left_strain(const float* F, float* X) {
 
 // The Drucker-Prager update of Sec. 3.2 step 4 (klar2016 return map, Hencky
 // elasticity) without an eigen-decomposition, for F F^T = I + X with the
-// largest row abs-sum of X at most 1/48 (every stretch within about 1% of 1).
+// largest row abs-sum xr of X at most 1/48 (every stretch within about 1% of 1).
 // The log strain is a matrix function of the left stretch V = (F F^T)^(1/2):
 // L = log V = log(I + X) / 2 has the eigenvectors U of F F^T and eigenvalues
 // eps_i = ln sigma_i, so tr eps = tr L and |eps^| = |dev L|_F.  The return map
 // moves eps along eps^ (or to 0 at the tip), which is L_new = L - k dev L (or
 // 0); then F_new = U diag(exp(eps_new - eps)) U^T F = exp(L_new - L) F and the
-// Hencky stress is 2 mu L_new + lam tr(L_new) I.  log(I + X) is its series
-// through X^4 (truncation below |X|^5 / 5 < 4e-8 |X|), exp(Y) its series
-// through Y^4 (|Y| <= 2 |L| <= 1/48: truncation below 5e-11 |Y|), both in
-// Horner form with products of commuting symmetric matrices.
-__device__ __forceinline__ void dp_small_strain(float* F, const float* X, float mu, float lam, float dpc,
-                                                float* tau) {
+// Hencky stress is 2 mu L_new + lam tr(L_new) I.  log(I + X) and exp(Y) are
+// their series through the d-th power in Horner form (products of commuting
+// symmetric matrices), with d chosen from xr (the spectral radius of X is at
+// most xr; L's is about xr/2, so that of Y, -L or a part of dev L, is below
+// xr): the log's truncation is below
+// xr^(d+1) / ((d+1)(1-xr)), i.e. below 4e-8 xr, for d = 2 up to xr = 3.4e-4,
+// d = 3 up to 5.4e-3 and d = 4 up to 1/48; the exponential's is smaller at the
+// same d.  One degree serves the warp (its largest), so neighbouring particles
+// do not diverge; the degree-4 case is the one this update always used.
+__device__ __forceinline__ int dp_lane_degree(float xr) { return xr <= 3.4e-4f ? 2 : xr <= 5.4e-3f ? 3 : 4; }
+
+// lane_deg: dp_lane_degree of the particle's xr
+__device__ __forceinline__ void dp_small_strain(float* F, const float* X, int lane_deg, float mu, float lam,
+                                                float dpc, float* tau) {
+  const int deg = __reduce_max_sync(__activemask(), lane_deg);
   float Z[6], W[6];
-  // log(I + X) = X (I - X (1/2 I - X (1/3 I - X / 4)))
+  // log(I + X) = X Q(X), Q = I - X/2 + X^2/3 - X^3/4 through degree deg:
+  // Z = I/(deg-1) - X/deg, then Z = I/k - X Z for k = deg-2 .. 1
+  const float za = deg == 4 ? 1.f / 3.f : deg == 3 ? 0.5f : 1.f;
+  const float zb = deg == 4 ? 0.25f : deg == 3 ? 1.f / 3.f : 0.5f;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) Z[q] = -0.25f * X[q] + (q < 3 ? 1.f / 3.f : 0.f);
-  const float c[2] = {0.5f, 1.f};
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
+  for (int q = 0; q < 6; ++q) Z[q] = -zb * X[q] + (q < 3 ? za : 0.f);
+  if (deg == 4) {
     sym_mul(X, Z, W);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) Z[q] = -W[q] + (q < 3 ? c[k] : 0.f);
+    for (int q = 0; q < 6; ++q) Z[q] = -W[q] + (q < 3 ? 0.5f : 0.f);
+  }
+  if (deg >= 3) {
+    sym_mul(X, Z, W);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Z[q] = -W[q] + (q < 3 ? 1.f : 0.f);
   }
   float L[6];
   sym_mul(X, Z, L);
@@ -467,15 +482,21 @@ __device__ __forceinline__ void dp_small_strain(float* F, const float* X, float 
     }
   }
   if (moved) {
-    // exp(Y) = I + Y (I + Y (1/2 I + Y (1/6 I + Y / 24)))
+    // exp(Y) = I + Y P(Y), P = I + Y/2 + Y^2/6 + Y^3/24 through degree deg:
+    // Z = I/(deg-1)! + Y/deg!, then Z = I/k! + Y Z for k = deg-2 .. 1
+    const float ea = deg == 4 ? 1.f / 6.f : deg == 3 ? 0.5f : 1.f;
+    const float eb = deg == 4 ? 1.f / 24.f : deg == 3 ? 1.f / 6.f : 0.5f;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) Z[q] = Y[q] * (1.f / 24.f) + (q < 3 ? 1.f / 6.f : 0.f);
-    const float e[2] = {0.5f, 1.f};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int q = 0; q < 6; ++q) Z[q] = Y[q] * eb + (q < 3 ? ea : 0.f);
+    if (deg == 4) {
       sym_mul(Y, Z, W);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) Z[q] = W[q] + (q < 3 ? e[k] : 0.f);
+      for (int q = 0; q < 6; ++q) Z[q] = W[q] + (q < 3 ? 0.5f : 0.f);
+    }
+    if (deg >= 3) {
+      sym_mul(Y, Z, W);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Z[q] = W[q] + (q < 3 ? 1.f : 0.f);
     }
     float Ex[6];
     sym_mul(Y, Z, Ex);

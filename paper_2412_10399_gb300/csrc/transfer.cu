@@ -947,13 +947,15 @@ __device__ __forceinline__ bool g2p_particle(const StepView& v, const SceneDev& 
   // Drucker-Prager at small stretch: matrix log/exp series, no eigen-
   // decomposition (such F is far from every float64 criterion)
   float Xs[6];
+  const float xr = mt.model == 1 ? left_strain(F, Xs) : 1.f;
   const bool small_dp = mt.model == 1 && s.gap_tol <= 0.f && s.j_tol < 0.9f && s.cond_tol < 0.9f &&
-                        left_strain(F, Xs) <= (1.f / 48.f);
+                        xr <= (1.f / 48.f);
+  const int sdeg = dp_lane_degree(xr);
   if (mt.model == 2) {
     // J-based fluid: volume ratio only, stress from J (no decomposition)
     fluid_update<float>(F, mt.E, mt.gamma, tau);
   } else if (small_dp) {
-    dp_small_strain(F, Xs, mu, lam, mt.dpc, tau);
+    dp_small_strain(F, Xs, sdeg, mu, lam, mt.dpc, tau);
   } else {
     // b = F F^T = U diag(sigma^2) U^T
     float bq[9], U[9], e[3], sg[3];

@@ -86,11 +86,14 @@ def test_p2g_grid_parity_dense_blocks(kernel):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("model,f_scale", [(S.FIXED_COROTATED, 0.08), (S.DRUCKER_PRAGER, 0.08),
-                                           (S.DRUCKER_PRAGER, 0.008)])
+                                           (S.DRUCKER_PRAGER, 0.008), (S.DRUCKER_PRAGER, 0.002),
+                                           (S.DRUCKER_PRAGER, 1e-4)])
 def test_one_step_particle_parity(kernel, model, f_scale):
     """f_scale 0.008 keeps F F^T within 1/32 of I for nearly every particle, so
     Drucker-Prager takes the small-stretch matrix-series update (elastic,
-    plastic and tip cases all occur); 0.08 takes the eigen-decomposition."""
+    plastic and tip cases all occur) through the fourth power; 0.002 and 1e-4
+    bring most warps to the third and second powers the series takes at
+    smaller strains; 0.08 takes the eigen-decomposition."""
     ck = need_gpu()
     sc, B, F = random_scene(5000, 32, 7, model=model, kernel=kernel, f_scale=f_scale)
     sim = _sim(ck, sc, B, F)
@@ -278,6 +281,7 @@ def test_fp64_pass_mixed_blocks_two_steps(model):
 
 
 @pytest.mark.parametrize("c,path", [(0.995, "series"), (0.9995, "series"), (1.002, "series"),
+                                    (0.99999, "series"), (1.0001, "series"),
                                     (0.9, "eigen"), (0.97, "eigen"), (1.05, "eigen"),
                                     (0.9, "fp64"), (1.05, "fp64")])
 def test_drucker_prager_isotropic_states_each_path(c, path):

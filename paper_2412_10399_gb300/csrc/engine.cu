@@ -521,9 +521,15 @@ ckmpm_status init_ctx(ckmpm_ctx* ctx, const ckmpm_config* cfg) {
   ctx->lc.transfer = ctx->transfer == CKMPM_TRANSFER_PIC ? 1 : ctx->transfer == CKMPM_TRANSFER_APIC_GRAD ? 2 : 0;
   if (const char* e = getenv("CKMPM_G2P_MINB")) ctx->lc.g2p_minb = std::max(4, std::min(6, atoi(e)));
   // two copies of the P2G accumulators are the faster choice for the
-  // quadratic twin (27-node stencils collide more), one for the compact kernel
+  // quadratic twin (27-node stencils collide more); the compact kernel keeps
+  // one copy and issues its components in the lane-rotated order.  Both
+  // round contributions by a fused multiply-add in blocks of >= 256 particles.
   ctx->lc.p2g_rep = ctx->kind == 1 ? 2 : 1;
+  ctx->lc.p2g_rot = ctx->kind == 1 ? 0 : 1;
+  ctx->lc.p2g_fma = 1;
   if (const char* e = getenv("CKMPM_P2G_REP")) ctx->lc.p2g_rep = atoi(e) == 2 ? 2 : 1;
+  if (const char* e = getenv("CKMPM_P2G_ROT")) ctx->lc.p2g_rot = atoi(e) != 0;
+  if (const char* e = getenv("CKMPM_P2G_FMA")) ctx->lc.p2g_fma = atoi(e) != 0;
   if (const char* e = getenv("CKMPM_SPLITS")) ctx->splits_override = std::max(1, std::min(8, atoi(e)));
   // steady steps run as CUDA graphs (CKMPM_GRAPHS=0 turns them off); the
   // legacy stream cannot be captured, so a context on it launches directly

@@ -15,6 +15,8 @@ struct LaunchCfg {
   int g2p_minb = 4;     // resident G2P warps per SM / 4 the register budget targets
   int transfer = 0;     // 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient
   int p2g_rep = 1;      // copies of the P2G shared accumulators (1 or 2)
+  int p2g_rot = 0;      // one copy: components in the lane-rotated order (1) or in order (0)
+  int p2g_fma = 0;      // APIC + MLS: fused-multiply-add rounding in blocks of >= 256 particles (1)
 };
 
 enum { LK_P2G = 0, LK_UPDATE = 1, LK_G2P = 2, LK_CLEAR = 3, LK_G2P_FP64 = 4, LK_G2P2G = 5, LK_LEFTOVER = 6 };

@@ -605,7 +605,23 @@ __device__ __forceinline__ void p2g_bounds(float inv_dx, float mass, float vx, f
          P2GBound<KIND>::wd * P2GBound<KIND>::dinv * rm * inv_dx;
 }
 
-template <int KIND>
+// FMA: a block of at least kP2GFmaCount particles has every scaled
+// contribution within 2^30 / count <= 2^22 in magnitude, where one fused
+// multiply-add with 1.5 * 2^23 rounds w * (...) to the nearest integer in the
+// low mantissa bits (the sum lies in [2^23, 2^24), whose spacing is 1): the
+// integer is the float's bits minus those of 1.5 * 2^23.  That takes the
+// conversion off the XU pipe; smaller blocks convert with __float2int_rn.
+constexpr uint32_t kP2GFmaCount = 256;
+
+template <bool FMA>
+__device__ __forceinline__ int p2g_fixed(float w, float val) {
+  if constexpr (FMA)
+    return __float_as_int(fmaf(w, val, 12582912.0f)) - 0x4B400000;
+  else
+    return __float2int_rn(w * val);
+}
+
+template <int KIND, bool FMA = false>
 __device__ __forceinline__ void p2g_scatter(const SceneDev& s, const MatDev* mats, uint32_t* err, const P2GPart& q,
                                             int ox, int oy, int oz, float Sm, float Sp, int (*sm)[Geo<KIND>::NS]) {
   Sten<KIND> st;
@@ -621,11 +637,114 @@ __device__ __forceinline__ void p2g_scatter(const SceneDev& s, const MatDev* mat
   const float ms = mass * Sm;
   const float px = mass * q.a.x * Sp, py = mass * q.a.y * Sp, pz = mass * q.a.z * Sp;
   for_nodes(st, [&](int j, float w, float dx, float dy, float dz) {
-    atomicAdd(&sm[0][j], __float2int_rn(w * ms));
-    atomicAdd(&sm[1][j], __float2int_rn(w * (px + A[0] * dx + A[1] * dy + A[2] * dz)));
-    atomicAdd(&sm[2][j], __float2int_rn(w * (py + A[3] * dx + A[4] * dy + A[5] * dz)));
-    atomicAdd(&sm[3][j], __float2int_rn(w * (pz + A[6] * dx + A[7] * dy + A[8] * dz)));
+    atomicAdd(&sm[0][j], p2g_fixed<FMA>(w, ms));
+    atomicAdd(&sm[1][j], p2g_fixed<FMA>(w, px + A[0] * dx + A[1] * dy + A[2] * dz));
+    atomicAdd(&sm[2][j], p2g_fixed<FMA>(w, py + A[3] * dx + A[4] * dy + A[5] * dz));
+    atomicAdd(&sm[3][j], p2g_fixed<FMA>(w, pz + A[6] * dx + A[7] * dy + A[8] * dz));
   });
+}
+
+// The same sums with the four components issued in a lane-rotated order.
+// A shared atomic instruction costs about the largest number of its lanes
+// that fall in one bank, and lanes on one address count like lanes on
+// distinct addresses of that bank: about three lanes of an instruction share
+// a cell and so every node of the stencil.  Here the instruction of slot c
+// (c = 0..3) adds component (c + rot) & 3, rot = (3 lane) & 3, so
+// neighbouring lanes of one cell write different planes (plane stride
+// kP2GRotPlane, 24 banks apart).  Every component is written as
+// w (R0 + R1 dx + R2 dy + R3 dz) with the rows R of the mass (m, 0, 0, 0) and
+// of the momenta (p_c, row c of A^); the lane's rows are permuted once per
+// particle by two selects each, so no register array is indexed at run
+// time.  pl[c] is the plane that instruction slot c writes.
+template <int KIND>
+struct P2GRotPlane {
+  static constexpr int value = ((Geo<KIND>::NS + 7) / 32) * 32 + 24;  // >= NS, = 24 mod 32
+};
+
+template <int KIND, bool FMA = false>
+__device__ __forceinline__ void p2g_scatter_rot(const SceneDev& s, const MatDev* mats, uint32_t* err,
+                                                const P2GPart& q, int ox, int oy, int oz, float Sm, float Sp,
+                                                int* const* pl, uint32_t rot) {
+  Sten<KIND> st;
+  if (!st.set(q.X.x * s.inv_dx, q.X.y * s.inv_dx, q.X.z * s.inv_dx, ox, oy, oz)) {
+    flag_error(err, CK_ERR_INTERNAL);
+    return;
+  }
+  const float M[9] = {q.a.w, q.b.x, q.b.y, q.b.z, q.b.w, q.c.x, q.c.y, q.c.z, q.c.w};
+  float A[9];
+  mul_dinv(st, M, s.inv_dx * Sp, A);
+  const float mass = mats[__float_as_uint(q.X.w)].mass;
+  const float R[4][4] = {{mass * Sm, 0.f, 0.f, 0.f},
+                         {mass * q.a.x * Sp, A[0], A[1], A[2]},
+                         {mass * q.a.y * Sp, A[3], A[4], A[5]},
+                         {mass * q.a.z * Sp, A[6], A[7], A[8]}};
+  const bool r1 = (rot & 1u) != 0u, r2 = (rot & 2u) != 0u;
+  float T[4][4], Q[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) T[c][e] = r1 ? R[(c + 1) & 3][e] : R[c][e];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Q[c][e] = r2 ? T[(c + 2) & 3][e] : T[c][e];
+  if constexpr (KIND == 0) {
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int E = g == 0 ? 5 : 6;
+      const int jb = (g == 0 ? 0 : 125) + (st.r[g][2] * E + st.r[g][1]) * E + st.r[g][0];
+      int* const b0 = pl[0] + jb;
+      int* const b1 = pl[1] + jb;
+      int* const b2 = pl[2] + jb;
+      int* const b3 = pl[3] + jb;
+#pragma unroll
+      for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+        for (int sy = 0; sy < 2; ++sy) {
+          const float wyz = st.w[g][1][sy] * st.w[g][2][sz];
+          const float dy = st.d[g][1][sy], dz = st.d[g][2][sz];
+          float e[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) e[c] = fmaf(Q[c][3], dz, fmaf(Q[c][2], dy, Q[c][0]));
+#pragma unroll
+          for (int sx = 0; sx < 2; ++sx) {
+            const int o = (sz * E + sy) * E + sx;
+            const float w = st.w[g][0][sx] * wyz;
+            const float dx = st.d[g][0][sx];
+            atomicAdd(b0 + o, p2g_fixed<FMA>(w, fmaf(Q[0][1], dx, e[0])));
+            atomicAdd(b1 + o, p2g_fixed<FMA>(w, fmaf(Q[1][1], dx, e[1])));
+            atomicAdd(b2 + o, p2g_fixed<FMA>(w, fmaf(Q[2][1], dx, e[2])));
+            atomicAdd(b3 + o, p2g_fixed<FMA>(w, fmaf(Q[3][1], dx, e[3])));
+          }
+        }
+    }
+  } else {
+    const int jb = (st.r[2] * 6 + st.r[1]) * 6 + st.r[0];
+    int* const b0 = pl[0] + jb;
+    int* const b1 = pl[1] + jb;
+    int* const b2 = pl[2] + jb;
+    int* const b3 = pl[3] + jb;
+#pragma unroll
+    for (int sz = 0; sz < 3; ++sz)
+#pragma unroll
+      for (int sy = 0; sy < 3; ++sy) {
+        const float wyz = st.w[1][sy] * st.w[2][sz];
+        const float dy = st.d[1][sy], dz = st.d[2][sz];
+        float e[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) e[c] = fmaf(Q[c][3], dz, fmaf(Q[c][2], dy, Q[c][0]));
+#pragma unroll
+        for (int sx = 0; sx < 3; ++sx) {
+          const int o = (sz * 6 + sy) * 6 + sx;
+          const float w = st.w[0][sx] * wyz;
+          const float dx = st.d[0][sx];
+          atomicAdd(b0 + o, p2g_fixed<FMA>(w, fmaf(Q[0][1], dx, e[0])));
+          atomicAdd(b1 + o, p2g_fixed<FMA>(w, fmaf(Q[1][1], dx, e[1])));
+          atomicAdd(b2 + o, p2g_fixed<FMA>(w, fmaf(Q[2][1], dx, e[2])));
+          atomicAdd(b3 + o, p2g_fixed<FMA>(w, fmaf(Q[3][1], dx, e[3])));
+        }
+      }
+  }
 }
 
 // PIC transfer (Sec. 4.3 with the kernel gradient): the state holds
@@ -703,15 +822,25 @@ struct P2GRep {
 };
 
 // TR: transfer, 0 APIC + MLS, 1 PIC, 2 APIC with the kernel gradient.
-template <int KIND, int TR, int REP>
+// ROT (APIC + MLS, one copy): components issued in the lane-rotated order of
+// p2g_scatter_rot, planes kP2GRotPlane apart.  FMA (APIC + MLS): blocks of
+// at least kP2GFmaCount particles round their contributions by p2g_fixed's
+// fused multiply-add instead of a conversion.
+template <int KIND, int TR, int REP, int ROT = 0, int FMA = 0>
 __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
   constexpr int NS = Geo<KIND>::NS;
-  constexpr int RS = P2GRep<KIND, REP>::stride;
+  static_assert(ROT == 0 || (REP == 1 && TR == 0), "the rotated order takes one copy and APIC + MLS");
+  static_assert(FMA == 0 || TR == 0, "fused-multiply-add rounding is built for APIC + MLS");
+  constexpr int PL = ROT ? P2GRotPlane<KIND>::value : NS;  // plane stride of the components
+  constexpr int RS = ROT ? 4 * PL : P2GRep<KIND, REP>::stride;
   constexpr uint32_t CAP = kP2GStage, C = kP2GStage / 32;
   static_assert(C % 2 == 1, "lane stride must be odd");
   static_assert(RS % 4 == 0, "copies must keep 16-byte alignment");
   __shared__ __align__(16) int small[REP * RS];
   int(*sm)[NS] = reinterpret_cast<int(*)[NS]>(small + (REP == 1 ? 0 : (int)(threadIdx.x & 1u) * RS));
+  const uint32_t rot = (threadIdx.x * 3u) & 3u;
+  int* const pl[4] = {small + ((0u + rot) & 3u) * PL, small + ((1u + rot) & 3u) * PL,
+                      small + ((2u + rot) & 3u) * PL, small + ((3u + rot) & 3u) * PL};
   __shared__ float4 sX[CAP], sA[CAP], sB[CAP], sC[CAP];
   constexpr uint32_t TCAP = TR == 2 ? CAP : 1;  // the stress term T (kernel-gradient APIC only)
   __shared__ float4 sT0[TCAP], sT1[TCAP];
@@ -774,8 +903,16 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
             const float4 t0 = sT0[i], t1 = sT1[i];
             const float T[9] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w, sT2[i]};
             p2g_scatter_grad<KIND>(s, v.mats, v.err, q, T, ox, oy, oz, Sm, Sp, sm);
+          } else if constexpr (ROT != 0) {
+            if (FMA && cnt >= kP2GFmaCount)
+              p2g_scatter_rot<KIND, true>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, pl, rot);
+            else
+              p2g_scatter_rot<KIND, false>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, pl, rot);
           } else {
-            p2g_scatter<KIND>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
+            if (FMA && cnt >= kP2GFmaCount)
+              p2g_scatter<KIND, true>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
+            else
+              p2g_scatter<KIND, false>(s, v.mats, v.err, q, ox, oy, oz, Sm, Sp, sm);
           }
         }
       }
@@ -788,7 +925,7 @@ __global__ void __launch_bounds__(kP2GWarp) k_p2g(StepView v) {
       int q[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        q[c] = small[c * NS + j];
+        q[c] = small[c * PL + j];
         if (REP == 2) q[c] += small[RS + c * NS + j];
       }
       if (q[0] != 0) {
@@ -1808,6 +1945,29 @@ __global__ void k_rekey(Pool P, uint32_t* key, uint32_t* cnt, uint32_t* bnd, con
 
 // ------------------------------------------------------------ host launchers
 
+// P2G of the APIC + MLS transfer: accumulator copies, component order and
+// rounding as the launch configuration asks.
+template <int KIND>
+static void launch_p2g_apic(const LaunchCfg& lc, StepView v) {
+  const int g = lc.sm_count * 32;
+  if (lc.p2g_rep == 2) {
+    if (lc.p2g_fma)
+      k_p2g<KIND, 0, 2, 0, 1><<<g, kP2GWarp, 0, lc.stream>>>(v);
+    else
+      k_p2g<KIND, 0, 2, 0, 0><<<g, kP2GWarp, 0, lc.stream>>>(v);
+  } else if (lc.p2g_rot) {
+    if (lc.p2g_fma)
+      k_p2g<KIND, 0, 1, 1, 1><<<g, kP2GWarp, 0, lc.stream>>>(v);
+    else
+      k_p2g<KIND, 0, 1, 1, 0><<<g, kP2GWarp, 0, lc.stream>>>(v);
+  } else {
+    if (lc.p2g_fma)
+      k_p2g<KIND, 0, 1, 0, 1><<<g, kP2GWarp, 0, lc.stream>>>(v);
+    else
+      k_p2g<KIND, 0, 1, 0, 0><<<g, kP2GWarp, 0, lc.stream>>>(v);
+  }
+}
+
 template <int KIND>
 static void launch_all(const LaunchCfg& lc, StepView v, int which) {
   switch (which) {
@@ -1816,10 +1976,8 @@ static void launch_all(const LaunchCfg& lc, StepView v, int which) {
         k_p2g<KIND, 1, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       else if (lc.transfer == 2)
         k_p2g<KIND, 2, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
-      else if (lc.p2g_rep == 2)
-        k_p2g<KIND, 0, 2><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
       else
-        k_p2g<KIND, 0, 1><<<lc.sm_count * 32, kP2GWarp, 0, lc.stream>>>(v);
+        launch_p2g_apic<KIND>(lc, v);
       break;
     // a wide grid: each CTA's block loop is short, so the dependent loads of
     // one block (list entry, scene, accumulators) overlap across CTAs

@@ -76,3 +76,53 @@ def test_oracle_maxima_match_closed_forms():
     assert float((t * O.K1(t)).max()) == pytest.approx(0.27751, abs=1e-5)
     assert c["wd"] <= 0.27751 + 1e-5 and c["wd"] >= 0.2765
     assert 13.9 <= c["dinv"] <= 14.05
+
+
+def _fixed_constants():
+    src = open(os.path.join(ROOT, "paper_2412_10399_gb300", "csrc", "transfer.cu")).read()
+    count = int(re.search(r"constexpr uint32_t kP2GFmaCount = (\d+);", src).group(1))
+    m = re.search(r"fmaf\(w, val, ([0-9.]+)f\)\) - (0x[0-9A-Fa-f]+);", src)
+    assert m, "the fused-multiply-add rounding of p2g_fixed was not found"
+    return count, float(m.group(1)), int(m.group(2), 16)
+
+
+def test_fma_rounding_is_round_to_nearest_within_its_range():
+    """p2g_fixed<true> rounds w * val by one float32 fused multiply-add with
+    1.5 * 2^23 and subtracts that constant's bits.  The FMA rounds the exact
+    value 1.5 * 2^23 + w val once; while |w val| <= 2^22 that value lies in
+    [2^23, 2^24], where the float32 numbers are exactly the integers, so the
+    result is w val rounded to the nearest integer (ties to even) plus
+    1.5 * 2^23, and its bits minus the constant's are that integer.  Checked
+    here with exact rational arithmetic on random float32 pairs and on ties
+    and the ends of the range."""
+    from fractions import Fraction
+
+    import numpy as np
+    count, magic, bits = _fixed_constants()
+    assert magic == 1.5 * 2.0 ** 23
+    assert bits == int(np.float32(magic).view(np.uint32))
+    # the scale maps count x bound to 2^30, so a block of `count` particles
+    # or more keeps every contribution within 2^22
+    assert 2.0 ** 30 / count <= 2.0 ** 22
+    rng = np.random.default_rng(0)
+    n = 20_000
+    w = rng.uniform(0.0, 1.003, n).astype(np.float32)
+    mag = 2.0 ** rng.uniform(-30.0, 22.0, n)
+    val = (np.where(rng.random(n) < 0.5, -1.0, 1.0) * mag).astype(np.float32)
+    pairs = [(float(a), float(b)) for a, b in zip(w, val)]
+    pairs += [(1.0, 2.0 ** 22), (1.0, -2.0 ** 22), (1.0, 0.5), (1.0, 1.5), (1.0, -2.5), (1.0, 0.0), (0.5, 3.0),
+              (1.0, 2.0 ** 22 - 0.5), (1.0, -(2.0 ** 22 - 0.5))]
+    two23, two24 = Fraction(2) ** 23, Fraction(2) ** 24
+    checked = 0
+    for a, b in pairs:
+        prod = Fraction(a) * Fraction(b)
+        if abs(prod) > Fraction(2) ** 22:
+            continue
+        exact = Fraction(magic) + prod
+        assert two23 <= exact <= two24
+        fma = round(exact)  # float32 rounding in [2^23, 2^24]: to the nearest integer, ties to even
+        assert fma == Fraction(int(np.float32(fma)))  # an integer there is a float32
+        got = int(np.float32(fma).view(np.int32)) - bits
+        assert got == round(prod), (a, b)
+        checked += 1
+    assert checked > n // 2

@@ -207,6 +207,26 @@ CKMPM_API ckmpm_status ckmpm_create(const ckmpm_scene* scene, int kernel, void* 
 /* Create an empty multi-scene context with the given capacities. */
 CKMPM_API ckmpm_status ckmpm_create_server(const ckmpm_config* cfg, ckmpm_ctx** out);
 
+/* Launch tuning read from the environment by ckmpm_create and
+ * ckmpm_create_server (once, at creation; unset means the default).  They
+ * change how the kernels are scheduled, never what they compute: results
+ * agree to float32 rounding.
+ *   CKMPM_GRAPHS=0        launch steady steps directly instead of replaying
+ *                         CUDA graphs
+ *   CKMPM_G2P_MINB=4|5|6  G2P register budget for the APIC + MLS transfer:
+ *                         16, 20 (default) or 24 resident warps per SM
+ *   CKMPM_P2G_REP=1|2     copies of the P2G shared accumulators (default: 1
+ *                         for the compact kernel, 2 for the quadratic twin)
+ *   CKMPM_P2G_ROT=0|1     with one copy, issue the four sums in order (0) or
+ *                         in the lane-rotated order (1; compact-kernel default)
+ *   CKMPM_P2G_FMA=0|1     APIC + MLS: round contributions to fixed point by a
+ *                         conversion (0) or, in blocks of 256 or more
+ *                         particles, by a fused multiply-add (1, default)
+ *   CKMPM_SPLITS=1..8     work units per particle block (default: chosen per
+ *                         step from the particle count)
+ *   CKMPM_CTAS_PER_SM=k   CTAs per SM of the kernel that clears the grid
+ *                         accumulators after ckmpm_probe_grids (default 8) */
+
 /* Admit a scene into a context (continuous batching: takes effect at the next
  * step; resident scenes keep running).  ENOMEM if any capacity would be
  * exceeded (nothing changes).  *scene_id receives the scene's id.

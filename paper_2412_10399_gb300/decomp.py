@@ -146,3 +146,63 @@ def migrate(fields: Dict[str, torch.Tensor], cell_x: torch.Tensor, rank: int, ra
         got = _exchange(sends, {p: (n_in[p],) + tuple(v.shape[1:]) for p in peers if n_in[p] > 0}, v, group)
         out[k] = torch.cat([v[keep]] + [got[p] for p in peers if p in got], 0)
     return out
+
+
+def layer_counts(cell_x: torch.Tensor, res: int, group=None) -> torch.Tensor:
+    """Particles per cell layer along x over all ranks (int64, length res):
+    each rank counts its own particles, then one sum over the group."""
+    c = torch.bincount(cell_x.clamp(0, res - 1).to(torch.int64), minlength=res)[:res].to(torch.int64)
+    if dist.is_initialized():
+        dist.all_reduce(c, op=dist.ReduceOp.SUM, group=group)
+    return c
+
+
+def balanced_slab_ranges(counts: torch.Tensor, world: int) -> List[Tuple[int, int]]:
+    """Cell ranges [lo, hi) along x in whole 4-cell blocks, one per rank, with
+    about the same number of particles each: counts holds the particles of
+    each cell layer (length res).  Boundary r is the block edge where the
+    running count first reaches r / world of the total, moved where needed so
+    that every rank keeps at least one block.  Where no boundary had to move,
+    a rank's load exceeds total / world by at most the particles of one block
+    layer.  With no particles the slabs are the even ones of slab_ranges."""
+    res = int(counts.numel())
+    nblk = -(-res // 4)
+    if world > nblk:
+        raise ValueError("more ranks than particle blocks along x")
+    per_blk = torch.zeros(nblk, dtype=torch.int64)
+    per_blk.index_add_(0, torch.arange(res) // 4, counts.to(torch.int64))
+    total = int(per_blk.sum())
+    if total == 0:
+        return slab_ranges(res, world)
+    cum = torch.cumsum(per_blk, 0)  # particles in blocks [0, b]
+    edges = [0]
+    for r in range(1, world):
+        target = (total * r + world - 1) // world
+        b = int(torch.searchsorted(cum, torch.tensor(target), right=False)) + 1  # first block edge with cum >= target
+        b = max(b, edges[-1] + 1)  # every rank keeps at least one block
+        b = min(b, nblk - (world - r))  # and leaves one for each rank above
+        edges.append(b)
+    edges.append(nblk)
+    return [(4 * edges[r], min(res, 4 * edges[r + 1])) for r in range(world)]
+
+
+def repartition(fields: Dict[str, torch.Tensor], cell_x: torch.Tensor, rank: int,
+                ranges: Sequence[Tuple[int, int]], group=None) -> Dict[str, torch.Tensor]:
+    """Move every particle to the rank whose slab holds its cell (any
+    distance: after new slab boundaries, where migrate only moves between
+    neighbours).  fields as for migrate.  Returns this rank's particles: the
+    ones it kept, then those received, in rank order."""
+    world = len(ranges)
+    own = owner_of_cells(cell_x, ranges)
+    peers = [p for p in range(world) if p != rank]
+    sel = {p: own == p for p in peers}
+    counts = _exchange({p: torch.tensor([int(sel[p].sum())], dtype=torch.int64) for p in peers},
+                       {p: (1,) for p in peers}, torch.zeros(1, dtype=torch.int64), group)
+    n_in = {p: int(counts[p][0]) for p in peers}
+    keep = own == rank
+    out = {}
+    for k, v in fields.items():  # the same field order on every rank
+        sends = {p: v[sel[p]] for p in peers if int(sel[p].sum()) > 0}
+        got = _exchange(sends, {p: (n_in[p],) + tuple(v.shape[1:]) for p in peers if n_in[p] > 0}, v, group)
+        out[k] = torch.cat([v[keep]] + [got[p] for p in peers if p in got], 0)
+    return out

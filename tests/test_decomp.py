@@ -22,9 +22,9 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _scene(kernel, model, n=1500, res=32, seed=81):
+def _scene(kernel, model, n=1500, res=32, seed=81, box=None):
     from paper_2412_10399_gb300 import scenes as S
-    x, v, B, F = S.random_state(n, res, seed, margin_cells=4.0, v_scale=40.0, f_scale=0.05)
+    x, v, B, F = S.random_state(n, res, seed, margin_cells=4.0, v_scale=40.0, f_scale=0.05, box=box)
     mat = S.Material(model, 1e5, 0.3, 1000.0, 30.0)
     sc = S.Scene("decomp", res, 1.0 / res, 1e-4, x, v, np.zeros(n, np.uint8), [mat], kernel=kernel)
     return sc, B, F
@@ -107,3 +107,101 @@ def test_slab_ranges_cover_the_domain_in_whole_blocks():
             assert all(r[i][1] == r[i + 1][0] for i in range(world - 1))
     with pytest.raises(ValueError):
         DC.slab_ranges(8, 3)
+
+
+def _balance_worker(rank, world, port, kernel, steps, n, res, box, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import ckmpm_oracle as O
+    sc, B, F = _scene(kernel, 1, n=n, res=res, box=box)
+    prm = O.params_from_scene(sc)
+    st_all = O.make_state(torch.from_numpy(sc.x), torch.from_numpy(sc.v), torch.from_numpy(B),
+                          torch.from_numpy(F), mat=torch.from_numpy(sc.mat.astype(np.int64)))
+    # start on even slabs: the particles crowd the low cells, mostly on rank 0
+    even = DC.slab_ranges(sc.res, world)
+    cell = torch.floor(st_all.x[:, 0] / prm.dx).to(torch.int64)
+    mine = DC.owner_of_cells(cell, even) == rank
+    f = {"x": st_all.x[mine], "v": st_all.v[mine], "B": st_all.B[mine], "F": st_all.F[mine],
+         "mat": st_all.mat[mine], "id": torch.arange(sc.n)[mine]}
+    n_even = int(mine.sum())
+    cx = torch.floor(f["x"][:, 0] / prm.dx).to(torch.int64)
+    counts = DC.layer_counts(cx, sc.res)
+    ranges = DC.balanced_slab_ranges(counts, world)
+    f = DC.repartition(f, cx, rank, ranges)
+    n_bal = int(f["id"].numel())
+    st = O.State(f["x"], f["v"], f["B"], f["F"], f["mat"])
+    ids = f["id"]
+    for _ in range(steps):
+        st = _step(st, prm, rank, ranges, O)
+        cx = torch.floor(st.x[:, 0] / prm.dx).to(torch.int64)
+        f = DC.migrate({"x": st.x, "v": st.v, "B": st.B, "F": st.F, "mat": st.mat, "id": ids}, cx, rank, ranges)
+        st = O.State(f["x"], f["v"], f["B"], f["F"], f["mat"])
+        ids = f["id"]
+    out[rank] = (ids.numpy(), st.x.numpy(), st.v.numpy(), st.F.numpy(), st.B.numpy(), n_even, n_bal,
+                 counts.numpy(), ranges)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,kernel,n,res,box", [(3, 0, 1200, 32, (4.0, 14.0)), (4, 1, 2000, 64, (4.0, 24.0))])
+def test_balanced_slabs_repartition_and_step_match_one_rank(world, kernel, n, res, box):
+    """A scene crowded into the low cells (4..14 of 32, 4..24 of 64) starts on
+    even slabs (most of it on the first rank), is repartitioned onto
+    particle-balanced slabs, then stepped with the halo exchanges and
+    migration: no rank holds more than n / world plus one block layer's
+    particles, and the union equals the single-rank run."""
+    from oracle import ckmpm_oracle as O
+    steps = 3
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_balance_worker, args=(world, port, kernel, steps, n, res, box, out), nprocs=world,
+                       join=True, start_method="spawn")
+    sc, B, F = _scene(kernel, 1, n=n, res=res, box=box)
+    counts = out[0][7]
+    assert counts.sum() == sc.n and all(np.array_equal(out[r][7], counts) for r in range(world))
+    ranges = out[0][8]
+    block = np.add.reduceat(counts, np.arange(0, sc.res, 4))
+    bound = -(-sc.n // world) + block.max()
+    even_max = max(out[r][5] for r in range(world))
+    bal_max = max(out[r][6] for r in range(world))
+    assert even_max > bound  # even slabs overload one rank
+    assert bal_max <= bound and min(out[r][6] for r in range(world)) > 0
+    assert sum(out[r][6] for r in range(world)) == sc.n
+    ref = O.run(O.make_state(torch.from_numpy(sc.x), torch.from_numpy(sc.v), torch.from_numpy(B),
+                             torch.from_numpy(F), mat=torch.from_numpy(sc.mat.astype(np.int64))),
+                O.params_from_scene(sc), steps)
+    got_ids = np.concatenate([out[r][0] for r in range(world)])
+    assert np.array_equal(np.sort(got_ids), np.arange(sc.n))
+    for j, field in ((1, ref.x), (2, ref.v), (3, ref.F), (4, ref.B)):
+        got = np.concatenate([out[r][j] for r in range(world)])[np.argsort(got_ids)]
+        want = field.numpy()
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+    assert all(b - a >= 4 for a, b in ranges)
+
+
+def test_balanced_slab_ranges_properties():
+    rng = np.random.default_rng(3)
+    for res in (16, 30, 64, 512):
+        for world in (1, 2, 3, 5, 8):
+            if world > -(-res // 4):
+                continue
+            counts = torch.from_numpy(rng.integers(0, 50, res) * (rng.random(res) < 0.6))
+            r = DC.balanced_slab_ranges(counts, world)
+            assert r[0][0] == 0 and r[-1][1] == res
+            assert all(a % 4 == 0 and a < b for a, b in r)
+            assert all(r[i][1] == r[i + 1][0] for i in range(world - 1))
+            loads = [int(counts[a:b].sum()) for a, b in r]
+            assert sum(loads) == int(counts.sum())
+            block = torch.zeros(-(-res // 4), dtype=torch.int64).index_add_(0, torch.arange(res) // 4, counts)
+            # no boundary had to move when every block edge is reachable: the load bound holds
+            if world <= int((block > 0).sum()):
+                assert max(loads) <= -(-int(counts.sum()) // world) + int(block.max())
+    # all particles in the last block: every rank still keeps one block
+    c = torch.zeros(16, dtype=torch.int64)
+    c[15] = 10
+    assert DC.balanced_slab_ranges(c, 4) == [(0, 4), (4, 8), (8, 12), (12, 16)]
+    assert DC.balanced_slab_ranges(torch.zeros(30, dtype=torch.int64), 3) == DC.slab_ranges(30, 3)
+    with pytest.raises(ValueError):
+        DC.balanced_slab_ranges(torch.ones(8, dtype=torch.int64), 3)

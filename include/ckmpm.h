@@ -239,6 +239,12 @@ CKMPM_API ckmpm_status ckmpm_admit(ckmpm_ctx* ctx, const ckmpm_scene* scene, int
 CKMPM_API ckmpm_status ckmpm_release(ckmpm_ctx* ctx, int scene_id);
 
 /* Enqueue n time steps of every resident scene on the context's stream.
+ * Each step is the pipeline of Sec. 3.2 on the dual grid of Sec. 4.2:
+ * binning of the particles by particle block (Sec. 5.1), P2G onto both grids
+ * (Sec. 4.3.1, 4.3.2, 4.4, 4.5), the grid update with gravity and sticky walls
+ * (Sec. 4.3.3), and G2P with the F update, the constitutive update and the
+ * advection (Sec. 4.3.4, 4.3.5; Sec. 3.2 steps 3-5); with CKMPM_STEP_G2P2G
+ * the G2P of step k and the P2G of step k + 1 run in one kernel (Sec. 5.1).
  * Asynchronous: device-side errors (EDOMAIN, ENONFINITE) surface at the next
  * ckmpm_sync / ckmpm_readback.  Returns EINVAL for n < 0, ECUDA on a launch
  * failure, or the sticky error of an earlier step.
@@ -254,12 +260,18 @@ CKMPM_API ckmpm_status ckmpm_step(ckmpm_ctx* ctx, int n);
 /* Wait for the context's stream and return the first device error (sticky). */
 CKMPM_API ckmpm_status ckmpm_sync(ckmpm_ctx* ctx);
 
-/* Run P2G and the grid update for the current state without advancing it,
- * so that GRID_M / GRID_P / GRID_V can be read back. */
+/* Run P2G (Sec. 4.3.1, 4.3.2, 4.4, 4.5) and the grid update (Sec. 4.3.3) for
+ * the current state without advancing it, so that GRID_M / GRID_P / GRID_V
+ * can be read back.  Enqueued on the context's stream like a step (the
+ * readback of a grid field synchronises); the next step first clears the
+ * probed accumulators. */
 CKMPM_API ckmpm_status ckmpm_probe_grids(ckmpm_ctx* ctx);
 
 /* Copy a field of one scene into dst (host or device), in the scene's
- * original particle order.  bytes must equal the field size exactly.
+ * original particle order.  bytes must equal the field size exactly.  B is
+ * the APIC matrix of Sec. 4.4 (the state keeps M = m B - dt V0 tau and B is
+ * recovered as (M + dt V0 tau(F)) / m), C = B D(x)^-1 with D of Sec. 4.4 at
+ * the particle's position.
  * Synchronises the stream.  EINVAL on a size mismatch.  A host dst goes
  * through ckmpm_readback_async + ckmpm_readback_wait (no allocation once the
  * staging slots have grown to the field's size). */

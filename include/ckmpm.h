@@ -150,7 +150,10 @@ typedef struct {
 } ckmpm_allocator;
 
 /* Capacities of a multi-scene context (a "server"): all resident scenes step
- * together in one launch per kernel over their concatenated block lists. */
+ * together in one launch per kernel over their concatenated block lists.
+ * Serving many scenes is an extension with no counterpart in the paper; each
+ * scene's step is the method's step above, with its own dx, dt, materials,
+ * gravity and walls. */
 typedef struct {
   int kernel;                  /* ckmpm_kernel | ckmpm_transfer | ckmpm_step_mode; fixed for the context */
   int64_t max_particles;       /* particle pool capacity */
@@ -227,8 +230,9 @@ CKMPM_API ckmpm_status ckmpm_create_server(const ckmpm_config* cfg, ckmpm_ctx** 
  *   CKMPM_CTAS_PER_SM=k   CTAs per SM of the kernel that clears the grid
  *                         accumulators after ckmpm_probe_grids (default 8) */
 
-/* Admit a scene into a context (continuous batching: takes effect at the next
- * step; resident scenes keep running).  ENOMEM if any capacity would be
+/* Admit a scene into a context (continuous batching, an extension with no
+ * counterpart in the paper: takes effect at the next step; resident scenes
+ * keep running).  ENOMEM if any capacity would be
  * exceeded (nothing changes).  *scene_id receives the scene's id.
  * Host x, v, mat are copied into a device staging buffer on the context's
  * stream (page-locked ones asynchronously; see Conventions). */

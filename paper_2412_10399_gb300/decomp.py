@@ -206,3 +206,28 @@ def repartition(fields: Dict[str, torch.Tensor], cell_x: torch.Tensor, rank: int
         got = _exchange(sends, {p: (n_in[p],) + tuple(v.shape[1:]) for p in peers if n_in[p] > 0}, v, group)
         out[k] = torch.cat([v[keep]] + [got[p] for p in peers if p in got], 0)
     return out
+
+
+def load_imbalance(counts: torch.Tensor, ranges: Sequence[Tuple[int, int]]) -> float:
+    """Largest rank's particle count over the mean (1.0 when balanced or empty)."""
+    loads = [int(counts[a:b].sum()) for a, b in ranges]
+    total = sum(loads)
+    return max(loads) * len(loads) / total if total else 1.0
+
+
+def rebalance(fields: Dict[str, torch.Tensor], cell_x: torch.Tensor, rank: int,
+              ranges: Sequence[Tuple[int, int]], res: int, tolerance: float = 0.1,
+              group=None) -> Tuple[Dict[str, torch.Tensor], List[Tuple[int, int]], bool]:
+    """Between steps: when the largest rank holds more than (1 + tolerance)
+    times the mean and particle-balanced slabs would hold less, move to those
+    slabs (repartition).  Every rank calls it with the same ranges; all take
+    the same decision from the summed layer counts.  Returns (fields, ranges,
+    whether they changed)."""
+    counts = layer_counts(cell_x, res, group)
+    now = load_imbalance(counts, ranges)
+    if now <= 1.0 + tolerance:
+        return fields, list(ranges), False
+    new = balanced_slab_ranges(counts, len(ranges))
+    if load_imbalance(counts, new) >= now:
+        return fields, list(ranges), False
+    return repartition(fields, cell_x, rank, new, group), new, True

@@ -217,3 +217,70 @@ def test_balanced_slab_ranges_properties():
     assert DC.balanced_slab_ranges(torch.zeros(30, dtype=torch.int64), 3) == DC.slab_ranges(30, 3)
     with pytest.raises(ValueError):
         DC.balanced_slab_ranges(torch.ones(8, dtype=torch.int64), 3)
+
+
+def _drift_worker(rank, world, port, steps, every, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import ckmpm_oracle as O
+    sc, B, F = _drift_scene()
+    prm = O.params_from_scene(sc)
+    st_all = O.make_state(torch.from_numpy(sc.x), torch.from_numpy(sc.v), torch.from_numpy(B),
+                          torch.from_numpy(F), mat=torch.from_numpy(sc.mat.astype(np.int64)))
+    cell = torch.floor(st_all.x[:, 0] / prm.dx).to(torch.int64)
+    ranges = DC.balanced_slab_ranges(DC.layer_counts(cell, sc.res) // world, world)  # same on every rank
+    mine = DC.owner_of_cells(cell, ranges) == rank
+    f = {"x": st_all.x[mine], "v": st_all.v[mine], "B": st_all.B[mine], "F": st_all.F[mine],
+         "mat": st_all.mat[mine], "id": torch.arange(sc.n)[mine]}
+    changes, worst = 0, 1.0
+    for k in range(steps):
+        st = O.State(f["x"], f["v"], f["B"], f["F"], f["mat"])
+        st = _step(st, prm, rank, ranges, O)
+        cx = torch.floor(st.x[:, 0] / prm.dx).to(torch.int64)
+        f = DC.migrate({"x": st.x, "v": st.v, "B": st.B, "F": st.F, "mat": st.mat, "id": f["id"]}, cx, rank, ranges)
+        if (k + 1) % every == 0:
+            cx = torch.floor(f["x"][:, 0] / prm.dx).to(torch.int64)
+            worst = max(worst, DC.load_imbalance(DC.layer_counts(cx, sc.res), ranges))
+            f, ranges, changed = DC.rebalance(f, cx, rank, ranges, sc.res, tolerance=0.1)
+            changes += int(changed)
+    out[rank] = (f["id"].numpy(), f["x"].numpy(), f["v"].numpy(), f["F"].numpy(), f["B"].numpy(), changes, worst,
+                 ranges)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _drift_scene():
+    """The crowded scene of the balance test moving along +x at 150 m/s
+    (0.48 cells per step; with the elastic wave speed the CFL number is 0.5)."""
+    sc, B, F = _scene(0, 0, n=1200, res=32, box=(4.0, 12.0))
+    sc.v = sc.v * 0.1 + np.array([150.0, 0.0, 0.0])
+    return sc, B, F
+
+
+def test_rebalance_follows_a_drifting_scene_and_matches_one_rank():
+    """Particles drift across the slab boundaries; every two steps the ranks
+    measure the imbalance and move to particle-balanced slabs when the
+    largest rank exceeds the mean by more than 10%.  At least one rebalance
+    happens, and after 16 steps (about 7.7 cells of drift) the union equals
+    the single-rank run."""
+    from oracle import ckmpm_oracle as O
+    world, steps, every = 3, 16, 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_drift_worker, args=(world, port, steps, every, out), nprocs=world, join=True,
+                       start_method="spawn")
+    sc, B, F = _drift_scene()
+    changes = {out[r][5] for r in range(world)}
+    assert len(changes) == 1 and changes.pop() >= 1  # every rank took the same decisions, at least once
+    assert all(out[r][7] == out[0][7] for r in range(world))
+    ref = O.run(O.make_state(torch.from_numpy(sc.x), torch.from_numpy(sc.v), torch.from_numpy(B),
+                             torch.from_numpy(F), mat=torch.from_numpy(sc.mat.astype(np.int64))),
+                O.params_from_scene(sc), steps)
+    got_ids = np.concatenate([out[r][0] for r in range(world)])
+    assert np.array_equal(np.sort(got_ids), np.arange(sc.n))
+    for j, field in ((1, ref.x), (2, ref.v), (3, ref.F), (4, ref.B)):
+        got = np.concatenate([out[r][j] for r in range(world)])[np.argsort(got_ids)]
+        want = field.numpy()
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
